@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Benchmark of the DDF hot path on one GB300 (or N independent replicas).
+
+One step = the whole path over the workload "lap7_128+elast3x3_64" (a 3-D
+7-point Laplacian on a 128^3 grid and a 3x3-block elasticity matrix on a 27-point
+stencil over 64^3 nodes): for each matrix A and its lower triangle L,
+    ddf_inspect(A, SpMV) -> ddf_spmv -> ddf_inspect(L, SpTRSV) -> ddf_sptrsv
+with CSR inputs and vectors already resident in HBM.  ``value`` is the
+executors' algorithmic bytes (plan statistics) moved per second of the whole
+step, inspection included.  Extra keys report each phase on its own.
+
+``--impl reference`` times the CPU oracle (plain sequential C, FP64) on the
+host cores over the same workload and prints the same line with
+``"impl": "reference"``.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "SpMV & SpTRSV GB/s as % of HBM roofline; mixed-precision vs FP64 speedup"
+WORKLOAD = ("lap7_128", "elast3x3_64")
+L2_FLUSH_BYTES = 256 << 20
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=float, default=1.0, help="grid scale (1.0 = the full workload)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def build_inputs(scale):
+    mats = []
+    for name in WORKLOAD:
+        a, lo, x, b = synth.workload(name, scale)
+        mats.append((name, a, lo, x, b))
+    return mats
+
+
+def csr_bytes(m):
+    return 4 * (m.n_rows + 1) + 12 * m.nnz
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2111_12243_gb300 as ddf
+    from paper_2111_12243_gb300 import build as ddf_build
+
+    ddf_build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    mats = build_inputs(args.scale)
+
+    def to_dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    D = []
+    for name, a, lo, x, b in mats:
+        D.append({
+            "name": name, "a": a, "lo": lo,
+            "A": (to_dev(a.rowptr), to_dev(a.colidx), to_dev(a.values)),
+            "L": (to_dev(lo.rowptr), to_dev(lo.colidx), to_dev(lo.values)),
+            "x": to_dev(x), "b": to_dev(b),
+            "y": torch.empty(a.n_rows, dtype=torch.float64, device=dev),
+            "xs": torch.empty(lo.n_rows, dtype=torch.float64, device=dev),
+        })
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    phases = ("inspect_spmv", "spmv", "inspect_sptrsv", "sptrsv")
+
+    def step(record):
+        evs = []
+        stats = []
+        for d in D:
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            e[0].record(stream)
+            pA = ddf.ddf_inspect(*d["A"], d["a"].n_cols, ddf.DDF_SPMV)
+            e[1].record(stream)
+            ddf.ddf_spmv(pA, d["x"], d["y"])
+            e[2].record(stream)
+            pL = ddf.ddf_inspect(*d["L"], d["lo"].n_cols, ddf.DDF_SPTRSV)
+            e[3].record(stream)
+            ddf.ddf_sptrsv(pL, d["b"], d["xs"])
+            e[4].record(stream)
+            if record:
+                stats.append((ddf.ddf_plan_stats(pA), ddf.ddf_plan_stats(pL)))
+            pA.destroy()
+            pL.destroy()
+            evs.append(e)
+        return evs, stats
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step(False)
+    torch.cuda.synchronize()
+    launches0 = ddf.ddf_kernel_launches()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    t0 = time.perf_counter()
+    steps = []
+    for _ in range(args.steps):
+        flush.zero_()
+        steps.append(step(True))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    launches = ddf.ddf_kernel_launches() - launches0
+
+    # per-phase times (ms) and bytes
+    ph = {(d["name"], p): [] for d in D for p in phases}
+    step_ms = []
+    for evs, _ in steps:
+        tot = 0.0
+        for d, e in zip(D, evs):
+            for i, p in enumerate(phases):
+                t = e[i].elapsed_time(e[i + 1])
+                ph[(d["name"], p)].append(t)
+                tot += t
+        step_ms.append(tot)
+    stats = steps[-1][1]
+    exec_b = sum(sa["bytes_exec"] + sl["bytes_exec"] for sa, sl in stats)
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = exec_b * world / (ms * 1e-3) / 1e9
+    hbm, peak_kind = peaks()
+
+    breakdown = {}
+    for (d, (sa, sl)) in zip(D, stats):
+        nm = d["name"]
+        t_spmv = float(np.mean(ph[(nm, "spmv")]))
+        t_trsv = float(np.mean(ph[(nm, "sptrsv")]))
+        breakdown[nm] = {
+            "inspect_spmv_ms": round(float(np.mean(ph[(nm, "inspect_spmv")])), 4),
+            "spmv_ms": round(t_spmv, 4),
+            "spmv_gbs": round(sa["bytes_exec"] / (t_spmv * 1e-3) / 1e9, 1),
+            "spmv_bytes": sa["bytes_exec"],
+            "inspect_sptrsv_ms": round(float(np.mean(ph[(nm, "inspect_sptrsv")])), 4),
+            "sptrsv_ms": round(t_trsv, 4),
+            "sptrsv_gbs": round(sl["bytes_exec"] / (t_trsv * 1e-3) / 1e9, 1),
+            "sptrsv_bytes": sl["bytes_exec"],
+            "depth": sl["depth"],
+            "codelets_spmv": sa["ncodelets"], "ops_spmv": sa["ops"],
+            "codelets_sptrsv": sl["ncodelets"], "ops_sptrsv": sl["ops"],
+        }
+    # dominant executor call (by time) for the roofline object
+    cand = []
+    for nm, bd in breakdown.items():
+        cand.append((bd["spmv_ms"], f"ddf_spmv[{nm}]", bd["spmv_bytes"]))
+        cand.append((bd["sptrsv_ms"], f"ddf_sptrsv[{nm}]", bd["sptrsv_bytes"]))
+    t_dom, dom, dom_bytes = max(cand)
+    achieved = dom_bytes / (t_dom * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
+                "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                "peak_source": f"{peak_kind} copy bandwidth"}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, D, ddf, torch, dev, stream, exec_b, world)
+
+    return {
+        "value": value, "ms_per_step": ms, "wall_s": wall, "launches": launches, "clocks": clk,
+        "breakdown": breakdown, "roofline": roofline, "e2e": e2e, "exec_bytes_per_step": exec_b,
+    }
+
+
+def run_e2e(args, D, ddf, torch, dev, stream, exec_b, world):
+    """Same step from pinned host buffers: CSR, x and b copied in, y and x read back."""
+    H = []
+    h2d = d2h = 0
+    for d in D:
+        a, lo = d["a"], d["lo"]
+        pin = lambda v: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()  # noqa: E731
+        H.append({"A": (pin(a.rowptr), pin(a.colidx), pin(a.values)),
+                  "L": (pin(lo.rowptr), pin(lo.colidx), pin(lo.values)),
+                  "x": pin(d["x"].cpu().numpy()), "b": pin(d["b"].cpu().numpy()),
+                  "y": torch.empty(a.n_rows, dtype=torch.float64).pin_memory(),
+                  "xs": torch.empty(lo.n_rows, dtype=torch.float64).pin_memory()})
+        h2d += csr_bytes(a) + csr_bytes(lo) + 8 * a.n_cols + 8 * lo.n_rows
+        d2h += 8 * a.n_rows + 8 * lo.n_rows
+
+    def step():
+        for d, h in zip(D, H):
+            pA = ddf.ddf_inspect(*h["A"], d["a"].n_cols, ddf.DDF_SPMV)
+            x = h["x"].to(dev, non_blocking=True)
+            y = torch.empty(d["a"].n_rows, dtype=torch.float64, device=dev)
+            ddf.ddf_spmv(pA, x, y)
+            h["y"].copy_(y, non_blocking=True)
+            pL = ddf.ddf_inspect(*h["L"], d["lo"].n_cols, ddf.DDF_SPTRSV)
+            b = h["b"].to(dev, non_blocking=True)
+            xs = torch.empty(d["lo"].n_rows, dtype=torch.float64, device=dev)
+            ddf.ddf_sptrsv(pL, b, xs)
+            h["xs"].copy_(xs, non_blocking=True)
+            pA.destroy()
+            pL.destroy()
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = float(np.mean(times))
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return {"value": round(exec_b * world / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+            "ms_per_step": round(ms, 3), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_step(mats):
+    import oracle
+    for name, a, lo, x, b in mats:
+        oracle.inspect(a, oracle.SPMV)
+        oracle.spmv(a, x)
+        oracle.inspect(lo, oracle.SPTRSV)
+        oracle.sptrsv(lo, b)
+
+
+def oracle_exec_bytes(mats):
+    """Executor algorithmic bytes of the oracle's plans, counted like the
+    library's plan statistics."""
+    import oracle
+    total = 0
+    for name, a, lo, x, b in mats:
+        for kind, m in ((oracle.SPMV, a), (oracle.SPTRSV, lo)):
+            p = oracle.inspect(m, kind)
+            r = p.records
+            lens = np.diff(m.rowptr.astype(np.int64))[p.perm] - (1 if kind == oracle.SPTRSV else 0)
+            cs = np.concatenate([[0], np.cumsum(lens)])
+            ops2 = sum(int(cs[q + mm] - cs[q]) for q, mm in zip(r[r[:, 1] == 2][:, 2], r[r[:, 1] == 2][:, 3]))
+            idx_rows = int((r[r[:, 1] == 2][:, 3] + 1).sum())
+            sent = int(r[r[:, 1] == 1][:, 4].sum())
+            perm_rows = int(r[r[:, 5] == 0][:, 3].sum())
+            pts = int(lens.sum())
+            n = m.n_rows
+            if kind == oracle.SPMV:
+                total += 8 * pts + 8 * m.n_cols + 8 * n + 4 * ops2 + 4 * idx_rows + 4 * sent + 64 * len(r)
+            else:
+                total += 8 * pts + 32 * n + 4 * ops2 + 4 * idx_rows + 4 * perm_rows + 4 * sent + 64 * len(r)
+    return total
+
+
+def run_oracle(mats, seconds, max_steps=None, warmup=0):
+    import oracle
+    oracle.build()
+    for _ in range(warmup):
+        oracle_step(mats)
+    times = []
+    t_end = time.perf_counter() + seconds
+    while True:
+        t0 = time.perf_counter()
+        oracle_step(mats)
+        times.append(time.perf_counter() - t0)
+        if max_steps is not None and len(times) >= max_steps:
+            break
+        if max_steps is None and time.perf_counter() > t_end:
+            break
+    return times
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        mats = build_inputs(args.scale)
+        times = run_oracle(mats, 0, max_steps=args.steps, warmup=args.warmup)
+        b = oracle_exec_bytes(mats)
+        ms = 1e3 * float(np.mean(times))
+        v = b / (ms * 1e-3) / 1e9
+        line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(ms, 2), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "+".join(WORKLOAD), "scale": args.scale},
+                "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                 "sample": "the full workload per step, sequential C oracle"},
+                "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    if world > 1:
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        torch.distributed.init_process_group(backend=backend)
+    r = run_ours(args, rank, world, local_rank)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        mats = build_inputs(args.scale)
+        times = run_oracle(mats, args.cpu_seconds)
+        b = oracle_exec_bytes(mats)
+        cv = b / float(np.mean(times)) / 1e9
+        cpu = {"value": round(cv, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"{len(times)} full steps of the workload (sequential C oracle, "
+                         f"{sum(times):.1f} s)", "exec_bytes_oracle_plan": b}
+    if rank == 0:
+        hbm, _ = peaks()
+        line = {
+            "metric": METRIC, "value": round(r["value"], 2), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r["ms_per_step"], 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "+".join(WORKLOAD), "scale": args.scale,
+                       "step": "inspect(A)+spmv+inspect(L)+sptrsv per matrix",
+                       "l2": "256 MB flush between steps; inputs larger than L2",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "frac_of_hbm": round(r["value"] / hbm, 4),
+            "roofline": r["roofline"],
+            "cpu_baseline": cpu,
+            "e2e": r["e2e"],
+            "gpu_launches": r["launches"],
+            "clocks": r["clocks"],
+            "breakdown": r["breakdown"],
+            "exec_bytes_per_step": r["exec_bytes_per_step"],
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

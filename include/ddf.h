@@ -1,0 +1,210 @@
+/*
+ * ddf.h - C ABI of the GB300 DDF library (libddf.so).
+ *
+ * DDF ("Vectorizing Sparse Matrix Codes with Dependency Driven Trace
+ * Analysis", Cetinic, Cheshmi, Dehnavi) is an inspector-executor method.  The
+ * inspector reads only the sparsity pattern of a CSR matrix and mines it for
+ * codelets (Sec. III, Alg. 1); the executor runs those codelets (Sec. IV-B).
+ * The paper's user calls are DDF_Inspector(A.pattern(), Kernel) and
+ * Kernel_Vectorized(clist, A, x, y) (Listing 2).  This library exposes the
+ * same split for the two kernels of the paper, SpMV (y = A x) and SpTRSV
+ * (L x = b, forward substitution on a lower triangle with its diagonal):
+ *
+ *     ddf_inspect(csr, kind)  -> device-resident plan (the codelet list)
+ *     ddf_spmv(plan, x, y)       ddf_sptrsv(plan, b, x)
+ *
+ * Conventions
+ *   - Plain C, no exceptions cross the ABI; every call returns ddf_status.
+ *   - Integer indices are int32 (rowptr, colidx); values and vectors are
+ *     IEEE binary64.  Row i of a CSR matrix holds columns colidx[rowptr[i] ..
+ *     rowptr[i+1]-1], strictly increasing, each in [0, n_cols).
+ *   - Pointers passed in are borrowed: they are read during the call (or, for
+ *     device pointers given to the execute calls, by the kernels that call
+ *     enqueues) and never freed by the library.  A plan owns every device
+ *     buffer it allocates; ddf_plan_destroy releases them.
+ *   - ddf_stream_t is a cudaStream_t (NULL = the legacy default stream).
+ *     The execute calls are asynchronous on that stream and do not
+ *     synchronise the host.  ddf_inspect synchronises the stream it is given
+ *     a few times (to read back sizes) before it returns.
+ *   - Argument and CSR validation errors are returned by the call.  Errors
+ *     that only the device can see (a dependency wait that ran out) are
+ *     latched in the plan's status word and returned by ddf_get_status.
+ *   - A plan is not safe for concurrent use from two streams: it carries
+ *     scratch state (the solve's work ticket and status word).
+ */
+#ifndef DDF_H
+#define DDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define DDF_API __attribute__((visibility("default")))
+#else
+#define DDF_API
+#endif
+
+typedef struct ddf_plan_s* ddf_plan_t;
+typedef void* ddf_stream_t;
+
+typedef enum {
+    DDF_OK = 0,
+    DDF_ERR_ARG = 1,            /* NULL pointer, negative size, bad option      */
+    DDF_ERR_NOT_SQUARE = 2,     /* SpTRSV needs n_rows == n_cols               */
+    DDF_ERR_UNSORTED = 3,       /* rowptr not monotone or columns not increasing */
+    DDF_ERR_OUT_OF_RANGE = 4,   /* a column outside [0, n_cols)                 */
+    DDF_ERR_NOT_LOWER = 5,      /* SpTRSV: an entry above the diagonal          */
+    DDF_ERR_MISSING_DIAG = 6,   /* SpTRSV: a row whose last entry is not L_ii    */
+    DDF_ERR_ZERO_DIAG = 7,      /* SpTRSV: L_ii == 0                            */
+    DDF_ERR_WRONG_KIND = 8,     /* execute call does not match the plan's kind  */
+    DDF_ERR_OOM = 9,            /* device allocation failed                      */
+    DDF_ERR_CUDA = 10,          /* a CUDA runtime call failed                    */
+    DDF_ERR_TIMEOUT = 11,       /* SpTRSV: a dependency wait exceeded its limit  */
+    DDF_ERR_NOT_CONVERGED = 12, /* reserved for iterative refinement            */
+    DDF_ERR_TOO_LARGE = 13      /* size beyond what an entry point supports      */
+} ddf_status;
+
+typedef enum { DDF_SPMV = 1, DDF_SPTRSV = 2 } ddf_kind;
+
+/* Codelet types (Sec. III-B): BLAS = f, g, h strided; PSC I = f, g strided and
+ * h(i0,i1) = h0 + delta*i0 + s[i1] with one offset array s for all rows;
+ * PSC II = the remaining runs, executed with per-nonzero column offsets. */
+typedef enum { DDF_BLAS = 0, DDF_PSC1 = 1, DDF_PSC2 = 2 } ddf_codelet_type;
+enum { DDF_ALLOW_BLAS = 1, DDF_ALLOW_PSC1 = 2, DDF_ALLOW_PSC2 = 4, DDF_ALLOW_ALL = 7 };
+
+/* A CSR matrix.  on_device != 0: the three arrays are device pointers on the
+ * current device; otherwise host pointers.  values may be NULL for
+ * ddf_inspect (pattern only, Listing 2); the plan's values are then set by
+ * ddf_update_values before the first execute call. */
+typedef struct {
+    int32_t n_rows, n_cols;
+    int64_t nnz;
+    const int32_t* rowptr;  /* [n_rows + 1], rowptr[0] = 0, rowptr[n_rows] = nnz */
+    const int32_t* colidx;  /* [nnz] */
+    const double* values;   /* [nnz] or NULL */
+    int32_t on_device;
+    int32_t reserved;
+} ddf_csr;
+
+/* Inspector and executor options; ddf_opts_default fills the defaults. */
+typedef struct {
+    int32_t window_t;       /* t: rows per mining region (Alg. 1, GetConsecutiveIterations), 1..512 */
+    int32_t allowed_types;  /* DDF_ALLOW_* mask; PSC II is required (default DDF_ALLOW_ALL)          */
+    int64_t w_op;           /* Eq. 1 weight of one operation |p|          (default 8 bytes)  */
+    int64_t w_codelet;      /* Eq. 1 per-codelet constant                 (default 32 bytes) */
+    int64_t w_index;        /* Eq. 1 weight of one offset-array entry     (default 4 bytes)  */
+    int64_t spin_cap_ns;    /* SpTRSV: longest wait on one dependency     (default 2e9 ns)   */
+    int32_t unit_nnz;       /* executor work unit: target nonzeros per warp (default 256)     */
+    int32_t reserved[9];
+} ddf_opts;
+
+/* Plan statistics (counts per codelet type are indexed by ddf_codelet_type). */
+typedef struct {
+    int32_t kind, n_rows, n_cols, depth;  /* depth = number of partitions (levels for SpTRSV) */
+    int64_t nnz;                          /* stored entries of the inspected matrix          */
+    int64_t points;                       /* iteration points (SpTRSV: off-diagonal entries) */
+    int64_t ncodelets[3];
+    int64_t ops[3];                       /* iteration points covered by each type (Fig. 8)  */
+    int64_t rows[3];                      /* rows covered by each type                        */
+    int64_t nunits;                       /* executor work units                              */
+    int64_t bytes_exec;                   /* algorithmic bytes of one execute call            */
+    int64_t max_row_len;
+    int64_t reserved[6];
+} ddf_plan_stats_t;
+
+/* Fill *o with the defaults listed above.  Never fails for a non-NULL o. */
+DDF_API void ddf_opts_default(ddf_opts* o);
+
+/*
+ * Inspector (Alg. 1).  Reads the pattern of A (and its values when present),
+ * validates it, and builds a device-resident plan on the current device:
+ *   kind == DDF_SPMV:   one partition with every row; codelets are runs of
+ *                       consecutive rows (Sec. IV-A, SpMV has no dependencies).
+ *   kind == DDF_SPTRSV: A must be square and lower triangular with every
+ *                       diagonal entry present, last in its row and nonzero.
+ *                       The dependency DAG's level sets are the partitions
+ *                       (findDependencies, partitionIterationSpace); codelets
+ *                       are runs of rows inside one level; the off-diagonal
+ *                       values are copied in that level order.
+ * o may be NULL (defaults).  On success *out receives the plan; on error *out
+ * is set to NULL and nothing is left allocated.  Synchronises stream s.
+ */
+DDF_API ddf_status ddf_inspect(const ddf_csr* A, ddf_kind kind, const ddf_opts* o, ddf_stream_t s,
+                       ddf_plan_t* out);
+
+/* Replace the plan's values with a new array of the same pattern (nnz entries
+ * in the original CSR order), without re-inspection.  values is a device
+ * pointer when on_device != 0.  SpTRSV: fails with DDF_ERR_ZERO_DIAG when a
+ * new diagonal entry is 0 (synchronises s in that case only to report it). */
+DDF_API ddf_status ddf_update_values(ddf_plan_t p, const double* values, int32_t on_device,
+                             ddf_stream_t s);
+
+/* SpMV executor: y = A x.  x [n_cols] and y [n_rows] are device pointers;
+ * y is overwritten (rows without entries get 0).  Launches one kernel per
+ * codelet type present (BLAS, PSC I, PSC II) on s. */
+DDF_API ddf_status ddf_spmv(ddf_plan_t p, const double* x, double* y, ddf_stream_t s);
+
+/* SpTRSV executor: solves L x = b by forward substitution.  b and x are
+ * device pointers of n_rows entries and must not overlap.  Rows are run
+ * level by level, codelets of one level together, levels linked by per-row
+ * ready flags (x itself: an entry is ready once it no longer holds the fill
+ * pattern written at the start of the call).  Every dependency wait is
+ * bounded by spin_cap_ns; a wait that runs out latches DDF_ERR_TIMEOUT in the
+ * plan's status word (read it with ddf_get_status) and the solve finishes
+ * with NaN in the affected rows instead of hanging. */
+DDF_API ddf_status ddf_sptrsv(ddf_plan_t p, const double* b, double* x, ddf_stream_t s);
+
+/* Synchronise s, then return and clear the plan's device status word. */
+DDF_API ddf_status ddf_get_status(ddf_plan_t p, ddf_stream_t s);
+
+/* Plan statistics (host struct).  Synchronous. */
+DDF_API ddf_status ddf_plan_stats(ddf_plan_t p, ddf_plan_stats_t* st);
+
+/*
+ * Export the plan in canonical form for checking:
+ *   records [ncodelets][12] int64: part, type, q0, m, n, f_str, rho, g_str,
+ *            gamma, h0, delta, sigma (n = -1 for PSC II; rho, gamma, delta,
+ *            sigma are 0 where undefined, e.g. for one-row codelets);
+ *   seq [n_rows] int32: the partition sequence (row at each position);
+ *   part_ptr [depth + 1] int32: first position of each partition;
+ *   gs [n_rows] int64: offset of each position's first value in the plan's
+ *            value layout (CSR order for SpMV, level order for SpTRSV).
+ * Any output pointer may be NULL to skip it; *ncodelets and *depth always
+ * receive the sizes.  Synchronous.
+ */
+DDF_API ddf_status ddf_plan_export(ddf_plan_t p, int64_t* records, int64_t* ncodelets, int32_t* seq,
+                           int32_t* part_ptr, int32_t* depth, int64_t* gs);
+
+/* Release every device buffer of the plan (stream-ordered on the stream the
+ * plan was inspected on).  NULL is ignored. */
+DDF_API void ddf_plan_destroy(ddf_plan_t p);
+
+/* Static description of a status code. */
+DDF_API const char* ddf_status_string(ddf_status st);
+
+/* Number of kernel launches the last execute call on this plan enqueued. */
+DDF_API int32_t ddf_last_launches(ddf_plan_t p);
+
+/* Total number of kernels this library has launched in the process so far
+ * (inspector, executors and their helpers).  Thread-safe. */
+DDF_API int64_t ddf_kernel_launches(void);
+
+/*
+ * Test hook for failure detection (not part of the method): overwrite one
+ * column of the plan's level-ordered SpTRSV copy so that the entry at
+ * position k of that copy names row `col`.  Pointing a row at a later row
+ * makes its dependency wait run out, which exercises the bounded waits and
+ * DDF_ERR_TIMEOUT without faulting the GPU.  Returns DDF_ERR_ARG when k or
+ * col is out of range.  Synchronous.
+ */
+DDF_API ddf_status ddf_debug_set_dependency(ddf_plan_t p, int64_t k, int32_t col);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDF_H */

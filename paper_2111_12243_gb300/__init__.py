@@ -1,0 +1,267 @@
+"""Python binding of libddf.so, the GB300 DDF library (include/ddf.h).
+
+Argument marshalling only: every step of inspection and execution runs in the
+library's CUDA kernels.  There is no CPU fallback; when the library has not
+been built, the first call raises ``DDFLibraryMissing``.  Build it with
+``paper_2111_12243_gb300.build.build()``.
+
+PyTorch provides device memory and streams: vectors passed to ``ddf_spmv``
+and ``ddf_sptrsv`` are contiguous float64 CUDA tensors, and the default stream
+argument is ``torch.cuda.current_stream()``.  CSR arrays given to
+``ddf_inspect`` may be CUDA tensors, CPU tensors or numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libddf.so")
+
+DDF_SPMV, DDF_SPTRSV = 1, 2
+DDF_BLAS, DDF_PSC1, DDF_PSC2 = 0, 1, 2
+DDF_ALLOW_BLAS, DDF_ALLOW_PSC1, DDF_ALLOW_PSC2, DDF_ALLOW_ALL = 1, 2, 4, 7
+STATUS = {0: "DDF_OK", 1: "DDF_ERR_ARG", 2: "DDF_ERR_NOT_SQUARE", 3: "DDF_ERR_UNSORTED",
+          4: "DDF_ERR_OUT_OF_RANGE", 5: "DDF_ERR_NOT_LOWER", 6: "DDF_ERR_MISSING_DIAG",
+          7: "DDF_ERR_ZERO_DIAG", 8: "DDF_ERR_WRONG_KIND", 9: "DDF_ERR_OOM", 10: "DDF_ERR_CUDA",
+          11: "DDF_ERR_TIMEOUT", 12: "DDF_ERR_NOT_CONVERGED", 13: "DDF_ERR_TOO_LARGE"}
+RECORD_FIELDS = ("part", "type", "q0", "m", "n", "f_str", "rho", "g_str", "gamma", "h0", "delta",
+                 "sigma")
+#: every symbol include/ddf.h declares
+EXPORTS = ("ddf_opts_default", "ddf_inspect", "ddf_update_values", "ddf_spmv", "ddf_sptrsv",
+           "ddf_get_status", "ddf_plan_stats", "ddf_plan_export", "ddf_plan_destroy",
+           "ddf_status_string", "ddf_last_launches", "ddf_kernel_launches",
+           "ddf_debug_set_dependency")
+
+
+class DDFLibraryMissing(ImportError):
+    pass
+
+
+class DDFError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = int(status)
+        super().__init__(f"{where}: {STATUS.get(self.status, self.status)} ({ddf_status_string(status)})")
+
+
+class ddf_csr(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int32), ("n_cols", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("colidx", ctypes.c_void_p), ("values", ctypes.c_void_p),
+                ("on_device", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ddf_opts(ctypes.Structure):
+    _fields_ = [("window_t", ctypes.c_int32), ("allowed_types", ctypes.c_int32),
+                ("w_op", ctypes.c_int64), ("w_codelet", ctypes.c_int64), ("w_index", ctypes.c_int64),
+                ("spin_cap_ns", ctypes.c_int64), ("unit_nnz", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 9)]
+
+
+class ddf_plan_stats_t(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n_rows", ctypes.c_int32), ("n_cols", ctypes.c_int32),
+                ("depth", ctypes.c_int32), ("nnz", ctypes.c_int64), ("points", ctypes.c_int64),
+                ("ncodelets", ctypes.c_int64 * 3), ("ops", ctypes.c_int64 * 3),
+                ("rows", ctypes.c_int64 * 3), ("nunits", ctypes.c_int64),
+                ("bytes_exec", ctypes.c_int64), ("max_row_len", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 6)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libddf.so (raises DDFLibraryMissing when it is not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise DDFLibraryMissing(f"{LIB_PATH} is missing: build it with "
+                                    "paper_2111_12243_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.ddf_opts_default.argtypes = [ctypes.POINTER(ddf_opts)]
+        L.ddf_opts_default.restype = None
+        L.ddf_inspect.argtypes = [ctypes.POINTER(ddf_csr), ctypes.c_int, ctypes.POINTER(ddf_opts), P,
+                                  ctypes.POINTER(P)]
+        L.ddf_update_values.argtypes = [P, P, I32, P]
+        L.ddf_spmv.argtypes = [P, P, P, P]
+        L.ddf_sptrsv.argtypes = [P, P, P, P]
+        L.ddf_get_status.argtypes = [P, P]
+        L.ddf_plan_stats.argtypes = [P, ctypes.POINTER(ddf_plan_stats_t)]
+        L.ddf_plan_export.argtypes = [P, P, ctypes.POINTER(I64), P, P, ctypes.POINTER(I32), P]
+        L.ddf_plan_destroy.argtypes = [P]
+        L.ddf_plan_destroy.restype = None
+        L.ddf_status_string.argtypes = [ctypes.c_int]
+        L.ddf_status_string.restype = ctypes.c_char_p
+        L.ddf_last_launches.argtypes = [P]
+        L.ddf_last_launches.restype = I32
+        L.ddf_kernel_launches.argtypes = []
+        L.ddf_kernel_launches.restype = I64
+        L.ddf_debug_set_dependency.argtypes = [P, I64, I32]
+        for name in ("ddf_inspect", "ddf_update_values", "ddf_spmv", "ddf_sptrsv", "ddf_get_status",
+                     "ddf_plan_stats", "ddf_plan_export", "ddf_debug_set_dependency"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    import torch
+    return ctypes.c_void_p(int(torch.cuda.current_stream().cuda_stream))
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise DDFError(st, where)
+
+
+def _ptr(a, dtype):
+    """(pointer, on_device, keep-alive) of a tensor / ndarray with the given numpy dtype."""
+    if a is None:
+        return None, 0, None
+    if hasattr(a, "is_cuda"):   # torch tensor
+        import torch
+        tdt = {np.int32: torch.int32, np.float64: torch.float64}[dtype]
+        if a.dtype != tdt:
+            raise TypeError(f"expected {tdt}, got {a.dtype}")
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), int(a.is_cuda), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data_as(ctypes.c_void_p), 0, arr
+
+
+def ddf_status_string(st: int) -> str:
+    return lib().ddf_status_string(int(st)).decode()
+
+
+def ddf_opts_default(**overrides) -> ddf_opts:
+    o = ddf_opts()
+    lib().ddf_opts_default(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+class Plan:
+    """A device-resident DDF plan (owns its device memory)."""
+
+    def __init__(self, handle, kind: int, n_rows: int, n_cols: int):
+        self._h = handle
+        self.kind = kind
+        self.n_rows = n_rows
+        self.n_cols = n_cols
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("plan has been destroyed")
+        return self._h
+
+    def destroy(self):
+        if self._h:
+            lib().ddf_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def ddf_inspect(rowptr, colidx, values, n_cols: int, kind: int, opts: ddf_opts | None = None,
+                stream=None) -> Plan:
+    """Inspector (Alg. 1) on a CSR matrix; ``values`` may be None (pattern only)."""
+    rp, dev_r, k1 = _ptr(rowptr, np.int32)
+    ci, dev_c, k2 = _ptr(colidx, np.int32)
+    va, dev_v, k3 = _ptr(values, np.float64)
+    if len({dev_r, dev_c} | ({dev_v} if values is not None else set())) != 1:
+        raise ValueError("rowptr, colidx and values must all be on the device or all on the host")
+    n_rows = int(len(rowptr)) - 1
+    nnz = int(len(colidx))
+    A = ddf_csr(n_rows, int(n_cols), nnz, rp, ci, va, dev_r, 0)
+    h = ctypes.c_void_p()
+    st = lib().ddf_inspect(ctypes.byref(A), int(kind), ctypes.byref(opts) if opts is not None else None,
+                           _stream(stream), ctypes.byref(h))
+    del k1, k2, k3
+    _check(st, "ddf_inspect")
+    return Plan(h, int(kind), n_rows, int(n_cols))
+
+
+def ddf_update_values(plan: Plan, values, stream=None):
+    va, dev, keep = _ptr(values, np.float64)
+    _check(lib().ddf_update_values(plan.handle, va, dev, _stream(stream)), "ddf_update_values")
+    del keep
+
+
+def _dev_vec(t, n, name):
+    if not (hasattr(t, "is_cuda") and t.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    import torch
+    if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name} must be a contiguous float64 tensor with {n} entries")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def ddf_spmv(plan: Plan, x, y, stream=None):
+    """y = A x on the device (asynchronous on the stream)."""
+    _check(lib().ddf_spmv(plan.handle, _dev_vec(x, plan.n_cols, "x"), _dev_vec(y, plan.n_rows, "y"),
+                          _stream(stream)), "ddf_spmv")
+
+
+def ddf_sptrsv(plan: Plan, b, x, stream=None):
+    """Solve L x = b on the device (asynchronous on the stream)."""
+    _check(lib().ddf_sptrsv(plan.handle, _dev_vec(b, plan.n_rows, "b"), _dev_vec(x, plan.n_rows, "x"),
+                            _stream(stream)), "ddf_sptrsv")
+
+
+def ddf_get_status(plan: Plan, stream=None) -> int:
+    """Synchronise, return and clear the plan's device status word."""
+    return int(lib().ddf_get_status(plan.handle, _stream(stream)))
+
+
+def ddf_plan_stats(plan: Plan) -> dict:
+    s = ddf_plan_stats_t()
+    _check(lib().ddf_plan_stats(plan.handle, ctypes.byref(s)), "ddf_plan_stats")
+    return {"kind": s.kind, "n_rows": s.n_rows, "n_cols": s.n_cols, "depth": s.depth, "nnz": s.nnz,
+            "points": s.points, "ncodelets": list(s.ncodelets), "ops": list(s.ops),
+            "rows": list(s.rows), "nunits": s.nunits, "bytes_exec": s.bytes_exec,
+            "max_row_len": s.max_row_len}
+
+
+def ddf_plan_export(plan: Plan) -> dict:
+    """Canonical plan: records (k, 12) int64, seq, part_ptr and gs (see ddf.h)."""
+    L = lib()
+    k = ctypes.c_int64(0)
+    d = ctypes.c_int32(0)
+    _check(L.ddf_plan_export(plan.handle, None, ctypes.byref(k), None, None, ctypes.byref(d), None),
+           "ddf_plan_export")
+    rec = np.zeros((k.value, 12), dtype=np.int64)
+    seq = np.zeros(max(plan.n_rows, 1), dtype=np.int32)
+    pp = np.zeros(d.value + 1, dtype=np.int32)
+    gs = np.zeros(max(plan.n_rows, 1), dtype=np.int64)
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check(L.ddf_plan_export(plan.handle, P(rec), ctypes.byref(k), P(seq), P(pp), ctypes.byref(d), P(gs)),
+           "ddf_plan_export")
+    return {"records": rec, "seq": seq[:plan.n_rows], "part_ptr": pp, "gs": gs[:plan.n_rows]}
+
+
+def ddf_plan_destroy(plan: Plan):
+    plan.destroy()
+
+
+def ddf_last_launches(plan: Plan) -> int:
+    return int(lib().ddf_last_launches(plan.handle))
+
+
+def ddf_kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(lib().ddf_kernel_launches())
+
+
+def ddf_debug_set_dependency(plan: Plan, k: int, col: int):
+    _check(lib().ddf_debug_set_dependency(plan.handle, int(k), int(col)), "ddf_debug_set_dependency")

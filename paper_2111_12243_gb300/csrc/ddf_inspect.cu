@@ -1,0 +1,921 @@
+// DDF inspector on the GPU (Alg. 1 of the paper).
+//
+//   computeAccessFunctions  implicit: position q of a partition sequence has
+//                           f(q) = seq[q], g(q,i1) = starts[q] + i1,
+//                           h(q,i1) = col[starts[q] + i1]           (Sec. III-A)
+//   findDependencies        SpTRSV: level of every row, longest path (k_levels)
+//   partitionIterationSpace SpTRSV: rows sorted by (level, row) (radix sort);
+//                           SpMV: one partition with every row      (Sec. IV-A)
+//   ComputeFOPD             first order partial differences per position and
+//                           between consecutive positions (k_features, Sec. III-D)
+//   GetConsecutiveIterations regions of t consecutive positions of a partition
+//   BLAS_first / PSCI_first / PSCII_first / min_cost / append
+//                           one thread per region (k_mine, k_emit)
+//
+// Every step is deterministic: counts come from per-region work followed by
+// prefix sums, and the level order from a stable radix sort.
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ddf_internal.cuh"
+
+namespace {
+
+enum : uint8_t { FL_HSTR = 1, FL_EQLEN = 2, FL_TRANS = 4, FL_LINK = 8 };
+enum { MK_NONE = -1 };
+
+// ---------------------------------------------------------------------------
+// validation
+// ---------------------------------------------------------------------------
+__global__ void k_validate(int32_t n, int32_t n_cols, int64_t nnz, const int32_t* __restrict__ rp,
+                           const int32_t* __restrict__ ci, const double* __restrict__ v, int kind,
+                           int32_t* __restrict__ err) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r == 0 && (rp[0] != 0 || (int64_t)rp[n] != nnz)) atomicMin(err, (int)DDF_ERR_UNSORTED);
+    if (r >= n) return;
+    int32_t a = rp[r], b = rp[r + 1];
+    if (a < 0 || b < a || (int64_t)b > nnz) {
+        atomicMin(err, (int)DDF_ERR_UNSORTED);
+        return;
+    }
+    int32_t prev = -1;
+    for (int32_t k = a; k < b; ++k) {
+        int32_t c = ci[k];
+        if (c < 0 || c >= n_cols) {
+            atomicMin(err, (int)DDF_ERR_OUT_OF_RANGE);
+            return;
+        }
+        if (c <= prev) {
+            atomicMin(err, (int)DDF_ERR_UNSORTED);
+            return;
+        }
+        prev = c;
+    }
+    if (kind == DDF_SPTRSV) {
+        if (b == a) atomicMin(err, (int)DDF_ERR_MISSING_DIAG);
+        else if (ci[b - 1] > r) atomicMin(err, (int)DDF_ERR_NOT_LOWER);
+        else if (ci[b - 1] != r) atomicMin(err, (int)DDF_ERR_MISSING_DIAG);
+        else if (v != nullptr && v[b - 1] == 0.0) atomicMin(err, (int)DDF_ERR_ZERO_DIAG);
+    }
+}
+
+__global__ void k_fill_i32(int32_t* __restrict__ a, int64_t n, int32_t v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+
+__global__ void k_iota_u32(int32_t* __restrict__ a, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = (int32_t)i;
+}
+
+__global__ void k_i64_to_i32(const int64_t* __restrict__ in, int32_t* __restrict__ out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int32_t)in[i];
+}
+
+// ---------------------------------------------------------------------------
+// findDependencies: level[i] = 1 + max level of its off-diagonal columns
+// ---------------------------------------------------------------------------
+constexpr int LEV_RPW = 32;                                   // rows per warp, in order
+constexpr int LEV_CHUNK = LEV_RPW * DDF_WARPS_PER_CTA;        // rows per CTA ticket
+
+// Bounded wait on a level written by another CTA: a few immediate polls, then
+// exponential backoff so that waiting warps do not flood L2 with requests.
+__device__ int32_t wait_level(const int32_t* p, int32_t* status, int64_t cap_ns) {
+    uint64_t t0 = ddf_globaltimer();
+    uint32_t it = 0, ns = 32;
+    while (true) {
+        int32_t v = ddf_ld_relaxed_s32(p);
+        if (v >= 0) return v;
+        ++it;
+        if (it > 4) {
+            __nanosleep(ns);
+            ns = min(ns * 2, 512u);
+        }
+        if ((it & 15u) == 0) {
+            if (ddf_ld_relaxed_s32(status) != 0) return 0;
+            if ((int64_t)(ddf_globaltimer() - t0) > cap_ns) {
+                ddf_set_status(status, DDF_ERR_TIMEOUT);
+                return 0;
+            }
+        }
+    }
+}
+
+// Bounded wait on a level written by another warp of this CTA.
+__device__ int32_t wait_level_smem(volatile int32_t* p, int32_t* status, int64_t cap_ns) {
+    uint64_t t0 = ddf_globaltimer();
+    uint32_t it = 0;
+    while (true) {
+        int32_t v = *p;
+        if (v >= 0) return v;
+        if ((++it & 255u) == 0) {
+            if (ddf_ld_relaxed_s32(status) != 0) return 0;
+            if ((int64_t)(ddf_globaltimer() - t0) > cap_ns) {
+                ddf_set_status(status, DDF_ERR_TIMEOUT);
+                return 0;
+            }
+        }
+    }
+}
+
+// Each CTA takes the next chunk of LEV_CHUNK consecutive rows from a ticket;
+// warp w computes rows [w*LEV_RPW, (w+1)*LEV_RPW) of the chunk in order.
+// Levels of the chunk's rows are also kept in shared memory: a dependency
+// inside the chunk (the common case for banded and stencil matrices) costs a
+// shared-memory read instead of an L2 round trip.  Every row waited on has a
+// smaller index, so it belongs to this CTA or to a CTA that already holds a
+// ticket and runs: the waits end.
+__global__ void __launch_bounds__(DDF_CTA_THREADS)
+k_levels(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int32_t* lev,
+         uint32_t* ticket, int32_t* maxlev, int32_t* status, int64_t cap_ns) {
+    __shared__ int32_t chunk;
+    __shared__ int32_t wmax[DDF_WARPS_PER_CTA];
+    __shared__ int32_t slev[LEV_CHUNK];
+    if (threadIdx.x == 0) chunk = (int32_t)atomicAdd(ticket, 1u);
+    for (int i = threadIdx.x; i < LEV_CHUNK; i += blockDim.x) slev[i] = -1;
+    __syncthreads();
+    volatile int32_t* vs = slev;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = (int64_t)chunk * LEV_CHUNK;
+    int32_t mymax = 0;
+    for (int rr = 0; rr < LEV_RPW; ++rr) {
+        const int64_t r = base + (int64_t)w * LEV_RPW + rr;
+        if (r >= n) break;
+        const int32_t a = rp[r], b = rp[r + 1] - 1;   // the diagonal is last: not a dependency
+        int32_t m = -1;
+        for (int32_t k = a + lane; k < b; k += 32) {
+            const int32_t j = ci[k];
+            int32_t lj;
+            if ((int64_t)j >= base) {
+                lj = vs[j - base];
+                if (lj < 0) lj = wait_level_smem(vs + (j - base), status, cap_ns);
+            } else {
+                lj = ddf_ld_relaxed_s32(lev + j);
+                if (lj < 0) lj = wait_level(lev + j, status, cap_ns);
+            }
+            m = max(m, lj);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) {
+            vs[r - base] = m + 1;
+            ddf_st_relaxed_s32(lev + r, m + 1);
+        }
+        mymax = max(mymax, m + 1);
+        __syncwarp();
+    }
+    if (lane == 0) wmax[w] = mymax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t t = 0;
+        for (int k = 0; k < DDF_WARPS_PER_CTA; ++k) t = max(t, wmax[k]);
+        atomicMax(maxlev, t);
+    }
+}
+
+// part_ptr[l] = first position of level l in the sorted order (every level
+// between 0 and depth-1 holds at least one row).
+__global__ void k_part_ptr(int32_t n, const uint32_t* __restrict__ ls, int32_t* __restrict__ pp,
+                           int32_t depth) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    if (q == 0) pp[depth] = n;
+    if (q == 0 || ls[q] != ls[q - 1]) pp[ls[q]] = (int32_t)q;
+}
+
+// ---------------------------------------------------------------------------
+// SpTRSV relayout: off-diagonal columns and values of the rows in level order
+// ---------------------------------------------------------------------------
+__global__ void k_rel_lens(int32_t n, const int32_t* __restrict__ perm, const int32_t* __restrict__ rp,
+                           int32_t* __restrict__ lens) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    int32_t r = perm[q];
+    lens[q] = rp[r + 1] - rp[r] - 1;
+}
+
+__global__ void k_rel_gather(int32_t n, const int32_t* __restrict__ perm, const int32_t* __restrict__ rp,
+                             const int32_t* __restrict__ ci, const double* __restrict__ vals,
+                             const int32_t* __restrict__ st, int32_t* __restrict__ col,
+                             double* __restrict__ val, double* __restrict__ dinv) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    int32_t r = perm[q];
+    int32_t a = rp[r], e = rp[r + 1] - 1, d = st[q];
+    if (col) for (int32_t k = a; k < e; ++k) col[d + (k - a)] = ci[k];
+    if (vals) {
+        for (int32_t k = a; k < e; ++k) val[d + (k - a)] = vals[k];
+        dinv[q] = 1.0 / vals[e];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// regions (GetConsecutiveIterations): windows of t positions of each partition
+// ---------------------------------------------------------------------------
+__global__ void k_region_counts(int32_t nparts, const int32_t* __restrict__ pp, int32_t t,
+                                int32_t* __restrict__ rc) {
+    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nparts) return;
+    int32_t sz = pp[l + 1] - pp[l];
+    rc[l] = (sz + t - 1) / t;
+}
+
+__global__ void k_region_fill(int32_t nparts, const int32_t* __restrict__ pp, int32_t t,
+                              const int64_t* __restrict__ roff, int32_t* __restrict__ ra,
+                              int32_t* __restrict__ rb, int32_t* __restrict__ rpart) {
+    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nparts) return;
+    int32_t b0 = pp[l], e0 = pp[l + 1];
+    int64_t o = roff[l];
+    for (int32_t a = b0; a < e0; a += t, ++o) {
+        ra[o] = a;
+        rb[o] = min(a + t, e0);
+        rpart[o] = (int32_t)l;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// ComputeFOPD
+// ---------------------------------------------------------------------------
+struct Feat {
+    const uint8_t* fl;
+    const int32_t *sig, *dF, *dG, *dH;
+    const int32_t* st;
+};
+
+__global__ void k_features(int32_t n, const int32_t* __restrict__ seq, const int32_t* __restrict__ st,
+                           const int32_t* __restrict__ col, const uint32_t* __restrict__ lsorted,
+                           uint8_t* __restrict__ fl, int32_t* __restrict__ sig, int32_t* __restrict__ dF,
+                           int32_t* __restrict__ dG, int32_t* __restrict__ dH) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    int32_t a = st[q], L = st[q + 1] - a;
+    const int32_t* h = col + a;
+    uint8_t f = 0;
+    int32_t s = 0;
+    bool ok = true;
+    if (L >= 2) {
+        s = h[1] - h[0];
+        for (int32_t i = 1; i + 1 < L; ++i)
+            if (h[i + 1] - h[i] != s) { ok = false; break; }
+    }
+    if (ok) f |= FL_HSTR;
+    int32_t df = 0, dg = 0, dh = 0;
+    bool link = q > 0 && (lsorted == nullptr || lsorted[q] == lsorted[q - 1]);
+    if (link) {
+        f |= FL_LINK;
+        int32_t ap = st[q - 1], Lp = a - ap;
+        df = seq ? seq[q] - seq[q - 1] : 1;
+        dg = a - ap;
+        if (L == Lp) {
+            f |= FL_EQLEN;
+            const int32_t* hp = col + ap;
+            bool t = true;
+            int32_t d0 = L > 0 ? h[0] - hp[0] : 0;
+            for (int32_t i = 1; i < L; ++i)
+                if (h[i] - hp[i] != d0) { t = false; break; }
+            if (t) {
+                f |= FL_TRANS;
+                dh = d0;
+            }
+        }
+    }
+    fl[q] = f;
+    sig[q] = s;
+    dF[q] = df;
+    dG[q] = dg;
+    dH[q] = dh;
+}
+
+// ---------------------------------------------------------------------------
+// mining strategies (one thread per region)
+// ---------------------------------------------------------------------------
+struct Weights {
+    int64_t op, cl, idx;
+};
+
+__device__ __forceinline__ int32_t ext_psc1(const Feat& F, int32_t q0, int32_t end) {
+    int32_t q1 = q0 + 1;
+    if (q1 >= end) return q1;
+    uint8_t f = F.fl[q1];
+    if (!(f & FL_EQLEN) || !(f & FL_TRANS)) return q1;
+    int32_t rf = F.dF[q1], rg = F.dG[q1], rh = F.dH[q1];
+    ++q1;
+    while (q1 < end) {
+        f = F.fl[q1];
+        if (!(f & FL_EQLEN) || !(f & FL_TRANS) || F.dF[q1] != rf || F.dG[q1] != rg || F.dH[q1] != rh)
+            break;
+        ++q1;
+    }
+    return q1;
+}
+
+__device__ __forceinline__ bool run_F(const Feat& F, int32_t q0, int32_t q1) {
+    for (int32_t q = q0 + 2; q < q1; ++q)
+        if (F.dF[q] != F.dF[q0 + 1]) return false;
+    return true;
+}
+
+__device__ __forceinline__ bool run_G(const Feat& F, int32_t q0, int32_t q1) {
+    for (int32_t q = q0 + 1; q < q1; ++q)
+        if (!(F.fl[q] & FL_EQLEN) || F.dG[q] != F.dG[q0 + 1]) return false;
+    return true;
+}
+
+// Eq. 1: c = w_op |p| + w_cl + w_idx (|s_f| + |s_g| + |s_h|)
+__device__ int64_t piece_cost(const Feat& F, int type, int32_t q0, int32_t q1, const Weights& w) {
+    int64_t m = q1 - q0;
+    int64_t p = (int64_t)F.st[q1] - F.st[q0];
+    int64_t sf = 0, sg = 0, sh = 0;
+    if (type == DDF_PSC1) sh = F.st[q0 + 1] - F.st[q0];
+    if (type == DDF_PSC2) {
+        sf = run_F(F, q0, q1) ? 0 : m;
+        sg = run_G(F, q0, q1) ? 0 : m;
+        sh = p;
+    }
+    return w.op * p + w.cl + w.idx * (sf + sg + sh);
+}
+
+struct Cov {
+    uint32_t b[DDF_MAX_T / 32];
+    __device__ void clear(int32_t len) {
+        for (int i = 0; i < (len + 31) / 32; ++i) b[i] = 0;
+    }
+    __device__ bool get(int32_t i) const { return (b[i >> 5] >> (i & 31)) & 1u; }
+    __device__ void set(int32_t i0, int32_t i1) {
+        for (int32_t i = i0; i < i1; ++i) b[i >> 5] |= 1u << (i & 31);
+    }
+};
+
+struct Sink {
+    int8_t* mark;   // NULL: cost only
+    int64_t cost;
+    int32_t pieces;
+    __device__ void put(const Feat& F, int type, int32_t q0, int32_t q1, const Weights& w) {
+        cost += piece_cost(F, type, q0, q1, w);
+        ++pieces;
+        if (mark) mark[q0] = (int8_t)type;
+    }
+};
+
+__device__ void leftovers(const Feat& F, const Cov& cov, int32_t a, int32_t b, const Weights& w,
+                          Sink& out) {
+    int32_t q = a;
+    while (q < b) {
+        if (cov.get(q - a)) { ++q; continue; }
+        int32_t u = q;
+        while (q < b && !cov.get(q - a)) ++q;
+        out.put(F, DDF_PSC2, u, q, w);
+    }
+}
+
+__device__ void blas_first(const Feat& F, int32_t a, int32_t b, int allowed, const Weights& w,
+                           Cov& cov, Sink& out) {
+    cov.clear(b - a);
+    int32_t q = a;
+    while (q < b) {
+        if (F.fl[q] & FL_HSTR) {
+            int32_t q1 = ext_psc1(F, q, b);
+            out.put(F, DDF_BLAS, q, q1, w);
+            cov.set(q - a, q1 - a);
+            q = q1;
+        } else {
+            ++q;
+        }
+    }
+    if (allowed & DDF_ALLOW_PSC1) {
+        q = a;
+        while (q < b) {
+            if (cov.get(q - a)) { ++q; continue; }
+            int32_t v = q;
+            while (v < b && !cov.get(v - a)) ++v;
+            int32_t u = q;
+            while (u < v) {
+                int32_t u1 = ext_psc1(F, u, v);
+                if (u1 - u >= 2) {
+                    out.put(F, DDF_PSC1, u, u1, w);
+                    cov.set(u - a, u1 - a);
+                    u = u1;
+                } else {
+                    ++u;
+                }
+            }
+            q = v;
+        }
+    }
+    leftovers(F, cov, a, b, w, out);
+}
+
+__device__ void psc1_first(const Feat& F, int32_t a, int32_t b, int allowed, const Weights& w,
+                           Cov& cov, Sink& out) {
+    cov.clear(b - a);
+    int32_t q = a;
+    while (q < b) {
+        int32_t q1 = ext_psc1(F, q, b);
+        if (q1 - q >= 2) {
+            int t = ((F.fl[q] & FL_HSTR) && (allowed & DDF_ALLOW_BLAS)) ? DDF_BLAS : DDF_PSC1;
+            out.put(F, t, q, q1, w);
+            cov.set(q - a, q1 - a);
+            q = q1;
+        } else {
+            ++q;
+        }
+    }
+    leftovers(F, cov, a, b, w, out);
+}
+
+// Pass 1: choose the strategy of least total cost (ties: BLAS_first, then
+// PSCI_first), write its piece starts into `mark` and the piece count.
+__global__ void k_mine(int64_t nreg, const int32_t* __restrict__ ra, const int32_t* __restrict__ rb,
+                       Feat F, int allowed, Weights w, int8_t* __restrict__ mark,
+                       int32_t* __restrict__ cnt) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nreg) return;
+    int32_t a = ra[r], b = rb[r];
+    Cov cov;
+    int64_t C[3];
+    int best = -1;
+    for (int s = 0; s < 3; ++s) {
+        if (s == 0 && !(allowed & DDF_ALLOW_BLAS)) continue;
+        if (s == 1 && !(allowed & DDF_ALLOW_PSC1)) continue;
+        Sink k{nullptr, 0, 0};
+        if (s == 0) blas_first(F, a, b, allowed, w, cov, k);
+        else if (s == 1) psc1_first(F, a, b, allowed, w, cov, k);
+        else k.put(F, DDF_PSC2, a, b, w);
+        C[s] = k.cost;
+        if (best < 0 || C[s] < C[best]) best = s;
+    }
+    for (int32_t q = a; q < b; ++q) mark[q] = (int8_t)MK_NONE;
+    Sink k{mark, 0, 0};
+    if (best == 0) blas_first(F, a, b, allowed, w, cov, k);
+    else if (best == 1) psc1_first(F, a, b, allowed, w, cov, k);
+    else k.put(F, DDF_PSC2, a, b, w);
+    cnt[r] = k.pieces;
+}
+
+// Pass 2 (cList.append): write the codelets of every region at its offset.
+__global__ void k_emit(int64_t nreg, const int32_t* __restrict__ ra, const int32_t* __restrict__ rb,
+                       const int32_t* __restrict__ rpart, Feat F, const int32_t* __restrict__ seq,
+                       const int32_t* __restrict__ col, const int8_t* __restrict__ mark,
+                       const int64_t* __restrict__ off, dcod* __restrict__ out) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nreg) return;
+    int32_t a = ra[r], b = rb[r];
+    int64_t o = off[r];
+    int32_t q = a;
+    while (q < b) {
+        int type = mark[q];
+        int32_t e = q + 1;
+        while (e < b && mark[e] == MK_NONE) ++e;
+        int32_t m = e - q;
+        int32_t L = F.st[q + 1] - F.st[q];
+        bool fs = run_F(F, q, e), gs = run_G(F, q, e);
+        dcod c;
+        c.q0 = q;
+        c.m = m;
+        c.n = (type == DDF_PSC2) ? -1 : L;
+        c.type = type;
+        c.part = rpart[r];
+        c.flags = (fs ? DC_F_STRIDED : 0) | (gs ? DC_G_STRIDED : 0);
+        c.f0 = seq ? seq[q] : q;
+        c.rho = (fs && m >= 2) ? F.dF[q + 1] : 0;
+        c.g0 = F.st[q];
+        c.gamma = (gs && m >= 2) ? F.dG[q + 1] : 0;
+        c.h0 = (type != DDF_PSC2 && L >= 1) ? col[F.st[q]] : 0;
+        c.delta = (type != DDF_PSC2 && m >= 2) ? F.dH[q + 1] : 0;
+        c.sigma = (type == DDF_BLAS && L >= 2) ? F.sig[q] : 0;
+        c.sref = F.st[q];
+        c.pad0 = c.pad1 = 0;
+        out[o++] = c;
+        q = e;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// executor work units
+// ---------------------------------------------------------------------------
+constexpr int64_t SPMV_WARP_SPAN = 4096;   // bytes of values one SpMV warp pass spans
+
+__device__ __forceinline__ int32_t pow2_ceil32(int32_t x) {
+    int32_t v = 1;
+    while (v < x && v < 32) v <<= 1;
+    return v;
+}
+
+// Units of one codelet.  BLAS / PSC I: rows split evenly, v = lanes per row.
+// PSC II: consecutive rows while the unit stays within unit_nnz points.
+// one_pass (SpTRSV): a unit is what one warp covers in a single pass, i.e.
+// 32 / v rows, so that a solve unit waits on its dependencies only once.
+template <bool WRITE>
+__device__ int32_t make_units(const dcod& c, int32_t ci, const int32_t* __restrict__ st,
+                              int32_t unit_nnz, bool one_pass, dunit* out) {
+    int32_t cnt = 0;
+    if (c.type != DDF_PSC2) {
+        int32_t n = c.n;
+        int32_t v, rows;
+        if (one_pass) {
+            v = pow2_ceil32(n > 0 ? n : 1);
+            rows = 32 / v;
+        } else {
+            // SpMV: the fewest lanes per row whose warp footprint (32/v rows of
+            // n values) stays within SPMV_WARP_SPAN bytes.  Fewer lanes per row
+            // means fewer shuffle-reduction additions: the FP64 pipe, not HBM,
+            // is the first limit of an FP64 SpMV on this part.
+            v = 1;
+            while (v < 32 && (int64_t)(32 / v) * n * 8 > SPMV_WARP_SPAN) v <<= 1;
+            int32_t rpw = 32 / v;
+            rows = rpw * max(1, (n > 0) ? unit_nnz / (rpw * n) : 32);
+        }
+        for (int32_t i = 0; i < c.m; i += rows) {
+            if (WRITE) out[cnt] = dunit{ci, i, min(i + rows, c.m), v};
+            ++cnt;
+        }
+        return cnt;
+    }
+    int32_t i = 0;
+    while (i < c.m) {
+        int32_t j = i;
+        if (one_pass) {
+            int32_t v = pow2_ceil32(max(st[c.q0 + i + 1] - st[c.q0 + i], 1));
+            j = i + 1;
+            while (j < c.m) {
+                int32_t v2 = max(v, pow2_ceil32(max(st[c.q0 + j + 1] - st[c.q0 + j], 1)));
+                if (v2 * (j - i + 1) > 32) break;
+                v = v2;
+                ++j;
+            }
+            if (WRITE) out[cnt] = dunit{ci, i, j, v};
+            ++cnt;
+            i = j;
+            continue;
+        }
+        int64_t pts = 0;
+        while (j < c.m && j - i < 256) {
+            int32_t L = st[c.q0 + j + 1] - st[c.q0 + j];
+            if (j > i && pts + L > unit_nnz) break;
+            pts += L;
+            ++j;
+        }
+        int32_t avg = (int32_t)((pts + (j - i) - 1) / (j - i));
+        if (WRITE) out[cnt] = dunit{ci, i, j, pow2_ceil32(avg > 0 ? avg : 1)};
+        ++cnt;
+        i = j;
+    }
+    return cnt;
+}
+
+__global__ void k_unit_counts(int64_t ncod, const dcod* __restrict__ cod, const int32_t* __restrict__ st,
+                              int32_t unit_nnz, int split_types, int32_t* __restrict__ c0,
+                              int32_t* __restrict__ c1, int32_t* __restrict__ c2) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncod) return;
+    dcod c = cod[i];
+    int32_t k = make_units<false>(c, (int32_t)i, st, unit_nnz, !split_types, nullptr);
+    if (!split_types) {
+        c0[i] = k;
+        return;
+    }
+    c0[i] = c.type == DDF_BLAS ? k : 0;
+    c1[i] = c.type == DDF_PSC1 ? k : 0;
+    c2[i] = c.type == DDF_PSC2 ? k : 0;
+}
+
+__global__ void k_unit_write(int64_t ncod, const dcod* __restrict__ cod, const int32_t* __restrict__ st,
+                             int32_t unit_nnz, int split_types, const int64_t* __restrict__ o0,
+                             const int64_t* __restrict__ o1, const int64_t* __restrict__ o2,
+                             dunit* __restrict__ u0, dunit* __restrict__ u1, dunit* __restrict__ u2) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncod) return;
+    dcod c = cod[i];
+    dunit* dst;
+    if (!split_types) dst = u0 + o0[i];
+    else if (c.type == DDF_BLAS) dst = u0 + o0[i];
+    else if (c.type == DDF_PSC1) dst = u1 + o1[i];
+    else dst = u2 + o2[i];
+    make_units<true>(c, (int32_t)i, st, unit_nnz, !split_types, dst);
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    template <typename T>
+    ddf_status get(T** p, int64_t n) {
+        ddf_status st = ddf_alloc(p, n, s);
+        if (!st && *p) ptrs.push_back((void*)*p);
+        return st;
+    }
+    ~Scratch() {
+        for (void* p : ptrs) (void)cudaFreeAsync(p, s);
+    }
+};
+
+template <typename T>
+ddf_status d2h(T* host, const T* dev, int64_t n, cudaStream_t s) {
+    if (n <= 0) return DDF_OK;
+    DDF_CUDA_TRY(cudaMemcpyAsync(host, dev, (size_t)n * sizeof(T), cudaMemcpyDeviceToHost, s));
+    DDF_CUDA_TRY(cudaStreamSynchronize(s));
+    return DDF_OK;
+}
+
+#define TRY(x)                         \
+    do {                               \
+        ddf_status t_ = (x);           \
+        if (t_ != DDF_OK) return t_;   \
+    } while (0)
+
+constexpr int TPB = 256;
+
+void fill_stats(ddf_plan_s* p, const std::vector<dcod>& hc) {
+    ddf_plan_stats_t& S = p->stats;
+    memset(&S, 0, sizeof(S));
+    S.kind = p->kind;
+    S.n_rows = p->n;
+    S.n_cols = p->n_cols;
+    S.depth = p->depth;
+    S.nnz = p->nnz;
+    S.points = p->npts;
+    int64_t psc2_nof = 0, s_entries = 0;
+    std::vector<int32_t> hst;
+    for (const dcod& c : hc) {
+        S.ncodelets[c.type]++;
+        S.rows[c.type] += c.m;
+        if (c.type == DDF_PSC1) s_entries += c.n;
+        if (c.type == DDF_PSC2 && !(c.flags & DC_F_STRIDED)) psc2_nof += c.m;
+    }
+    S.nunits = p->nunits[0] + p->nunits[1] + p->nunits[2];
+    (void)psc2_nof;
+    (void)s_entries;
+}
+
+}  // namespace
+
+// Build the plan from device copies of the CSR arrays (rowptr/colidx/values,
+// values may be NULL).  SpMV keeps the three arrays as its value layout.
+ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* colidx,
+                          const double* values, cudaStream_t s) {
+    const int32_t n = p->n;
+    const int kind = p->kind;
+    Scratch tmp{s, {}};
+    int32_t* err = nullptr;
+    TRY(tmp.get(&err, 1));
+    int32_t big = 0x7fffffff;
+    DDF_CUDA_TRY(cudaMemcpyAsync(err, &big, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    k_validate<<<ddf_grid(n + 1, TPB), TPB, 0, s>>>(n, p->n_cols, p->nnz, rowptr, colidx, values, kind, err);
+    ddf_count_launch();
+    DDF_CUDA_TRY(cudaGetLastError());
+    int32_t herr = 0;
+    TRY(d2h(&herr, err, 1, s));
+    if (herr != 0x7fffffff) return (ddf_status)herr;
+
+    const int32_t* seq = nullptr;        // identity for SpMV
+    uint32_t* lsorted = nullptr;         // level of each position (SpTRSV)
+    if (kind == DDF_SPMV) {
+        p->starts = const_cast<int32_t*>(rowptr);
+        p->col = const_cast<int32_t*>(colidx);
+        p->val = const_cast<double*>(values);
+        p->depth = n > 0 ? 1 : 0;
+        p->npts = p->nnz;
+        TRY(ddf_alloc(&p->part_ptr, 2, s));
+        int32_t hp[2] = {0, n};
+        DDF_CUDA_TRY(cudaMemcpyAsync(p->part_ptr, hp, sizeof(hp), cudaMemcpyHostToDevice, s));
+        DDF_CUDA_TRY(cudaStreamSynchronize(s));
+    } else {
+        // findDependencies: sync-free levels
+        int32_t* lev = nullptr;
+        uint32_t* tick = nullptr;
+        int32_t* maxlev = nullptr;
+        TRY(tmp.get(&lev, n));
+        TRY(tmp.get(&tick, 1));
+        TRY(tmp.get(&maxlev, 1));
+        k_fill_i32<<<ddf_grid(n, TPB, 4096), TPB, 0, s>>>(lev, n, -1);
+        ddf_count_launch();
+        DDF_CUDA_TRY(cudaMemsetAsync(tick, 0, sizeof(uint32_t), s));
+        DDF_CUDA_TRY(cudaMemsetAsync(maxlev, 0, sizeof(int32_t), s));
+        DDF_CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(int32_t), s));
+        if (n > 0) {
+            k_levels<<<ddf_grid(n, LEV_CHUNK), DDF_CTA_THREADS, 0, s>>>(n, rowptr, colidx, lev, tick, maxlev,
+                                                                       p->status, p->opts.spin_cap_ns);
+            ddf_count_launch();
+        }
+        DDF_CUDA_TRY(cudaGetLastError());
+        int32_t hmax = 0, hstat = 0;
+        TRY(d2h(&hmax, maxlev, 1, s));
+        TRY(d2h(&hstat, p->status, 1, s));
+        if (hstat) return (ddf_status)hstat;
+        p->depth = n > 0 ? hmax + 1 : 0;   // hmax is the largest level
+        // partitionIterationSpace: rows sorted by (level, row)
+        TRY(ddf_alloc(&p->seq, n, s));
+        TRY(tmp.get(&lsorted, n));
+        DDF_CUDA_TRY(cudaMemcpyAsync(lsorted, lev, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+        k_iota_u32<<<ddf_grid(n, TPB, 4096), TPB, 0, s>>>(p->seq, n);
+        ddf_count_launch();
+        TRY(ddf_radix_sort_u32(lsorted, p->seq, n, (uint32_t)(p->depth > 0 ? p->depth - 1 : 0), s));
+        TRY(ddf_alloc(&p->part_ptr, (int64_t)p->depth + 1, s));
+        if (n > 0) {
+            k_part_ptr<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, lsorted, p->part_ptr, p->depth);
+            ddf_count_launch();
+        }
+        else DDF_CUDA_TRY(cudaMemsetAsync(p->part_ptr, 0, sizeof(int32_t), s));
+        // level-ordered copy of the off-diagonal entries
+        int32_t* lens = nullptr;
+        int64_t* st64 = nullptr;
+        TRY(tmp.get(&lens, n));
+        TRY(tmp.get(&st64, (int64_t)n + 1));
+        if (n > 0) {
+            k_rel_lens<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, p->seq, rowptr, lens);
+            ddf_count_launch();
+        }
+        TRY(ddf_scan_i32_to_i64(lens, st64, n, s));
+        int64_t npts = 0;
+        TRY(d2h(&npts, st64 + n, 1, s));
+        p->npts = npts;
+        TRY(ddf_alloc(&p->starts, (int64_t)n + 1, s));
+        k_i64_to_i32<<<ddf_grid(n + 1, TPB, 4096), TPB, 0, s>>>(st64, p->starts, (int64_t)n + 1);
+        ddf_count_launch();
+        TRY(ddf_alloc(&p->col, npts, s));
+        TRY(ddf_alloc(&p->val, npts, s));
+        TRY(ddf_alloc(&p->dinv, n, s));
+        if (n > 0) {
+            k_rel_gather<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, p->seq, rowptr, colidx, values, p->starts,
+                                                        p->col, p->val, p->dinv);
+            ddf_count_launch();
+        }
+        DDF_CUDA_TRY(cudaGetLastError());
+        // keep the inspected rowptr for ddf_update_values
+        p->orig_rowptr = const_cast<int32_t*>(rowptr);
+    }
+    p->has_values = values != nullptr;
+
+    // regions
+    int32_t nparts = p->depth;
+    int32_t t = p->opts.window_t;
+    int32_t* rc = nullptr;
+    int64_t* roff = nullptr;
+    TRY(tmp.get(&rc, nparts));
+    TRY(tmp.get(&roff, (int64_t)nparts + 1));
+    if (nparts > 0) {
+        k_region_counts<<<ddf_grid(nparts, TPB), TPB, 0, s>>>(nparts, p->part_ptr, t, rc);
+        ddf_count_launch();
+    }
+    TRY(ddf_scan_i32_to_i64(rc, roff, nparts, s));
+    int64_t nreg = 0;
+    TRY(d2h(&nreg, roff + nparts, 1, s));
+    int32_t *ra = nullptr, *rb = nullptr, *rpart = nullptr;
+    TRY(tmp.get(&ra, nreg));
+    TRY(tmp.get(&rb, nreg));
+    TRY(tmp.get(&rpart, nreg));
+    if (nparts > 0) {
+        k_region_fill<<<ddf_grid(nparts, TPB), TPB, 0, s>>>(nparts, p->part_ptr, t, roff, ra, rb, rpart);
+        ddf_count_launch();
+    }
+
+    // ComputeFOPD
+    uint8_t* fl = nullptr;
+    int32_t *sig = nullptr, *dF = nullptr, *dG = nullptr, *dH = nullptr;
+    TRY(tmp.get(&fl, n));
+    TRY(tmp.get(&sig, n));
+    TRY(tmp.get(&dF, n));
+    TRY(tmp.get(&dG, n));
+    TRY(tmp.get(&dH, n));
+    seq = p->seq;
+    if (n > 0) {
+        k_features<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, seq, p->starts, p->col, lsorted, fl, sig, dF, dG, dH);
+        ddf_count_launch();
+    }
+    DDF_CUDA_TRY(cudaGetLastError());
+    Feat F{fl, sig, dF, dG, dH, p->starts};
+    Weights w{p->opts.w_op, p->opts.w_codelet, p->opts.w_index};
+
+    // mining and append
+    int8_t* mark = nullptr;
+    int32_t* cnt = nullptr;
+    int64_t* off = nullptr;
+    TRY(tmp.get(&mark, n));
+    TRY(tmp.get(&cnt, nreg));
+    TRY(tmp.get(&off, nreg + 1));
+    if (nreg > 0) {
+        k_mine<<<ddf_grid(nreg, 64), 64, 0, s>>>(nreg, ra, rb, F, p->opts.allowed_types, w, mark, cnt);
+        ddf_count_launch();
+    }
+    DDF_CUDA_TRY(cudaGetLastError());
+    TRY(ddf_scan_i32_to_i64(cnt, off, nreg, s));
+    int64_t ncod = 0;
+    TRY(d2h(&ncod, off + nreg, 1, s));
+    p->ncod = ncod;
+    TRY(ddf_alloc(&p->cod, ncod, s));
+    if (nreg > 0) {
+        k_emit<<<ddf_grid(nreg, 64), 64, 0, s>>>(nreg, ra, rb, rpart, F, seq, p->col, mark, off, p->cod);
+        ddf_count_launch();
+    }
+    DDF_CUDA_TRY(cudaGetLastError());
+
+    // executor units
+    int split = kind == DDF_SPMV;
+    int32_t *c0 = nullptr, *c1 = nullptr, *c2 = nullptr;
+    int64_t *o0 = nullptr, *o1 = nullptr, *o2 = nullptr;
+    TRY(tmp.get(&c0, ncod));
+    TRY(tmp.get(&o0, ncod + 1));
+    if (split) {
+        TRY(tmp.get(&c1, ncod));
+        TRY(tmp.get(&c2, ncod));
+        TRY(tmp.get(&o1, ncod + 1));
+        TRY(tmp.get(&o2, ncod + 1));
+    }
+    if (ncod > 0) {
+        k_unit_counts<<<ddf_grid(ncod, TPB), TPB, 0, s>>>(ncod, p->cod, p->starts, p->opts.unit_nnz,
+                                                         split, c0, c1, c2);
+        ddf_count_launch();
+    }
+    DDF_CUDA_TRY(cudaGetLastError());
+    TRY(ddf_scan_i32_to_i64(c0, o0, ncod, s));
+    if (split) {
+        TRY(ddf_scan_i32_to_i64(c1, o1, ncod, s));
+        TRY(ddf_scan_i32_to_i64(c2, o2, ncod, s));
+    }
+    int64_t tot[3] = {0, 0, 0};
+    TRY(d2h(&tot[0], o0 + ncod, 1, s));
+    if (split) {
+        TRY(d2h(&tot[1], o1 + ncod, 1, s));
+        TRY(d2h(&tot[2], o2 + ncod, 1, s));
+    }
+    for (int k = 0; k < 3; ++k) {
+        p->nunits[k] = tot[k];
+        TRY(ddf_alloc(&p->units[k], tot[k], s));
+    }
+    if (ncod > 0) {
+        k_unit_write<<<ddf_grid(ncod, TPB), TPB, 0, s>>>(ncod, p->cod, p->starts, p->opts.unit_nnz, split,
+                                                        o0, o1, o2, p->units[0], p->units[1], p->units[2]);
+        ddf_count_launch();
+    }
+    DDF_CUDA_TRY(cudaGetLastError());
+
+    p->stats_ready = 0;
+    DDF_CUDA_TRY(cudaStreamSynchronize(s));
+    return DDF_OK;
+}
+
+// Plan statistics, computed on first request from a host copy of the
+// descriptors and the starts array (not part of inspection).
+ddf_status ddf_compute_stats(ddf_plan_s* p) {
+    cudaStream_t s = p->stream;
+    const int32_t n = p->n;
+    const int64_t ncod = p->ncod;
+    std::vector<dcod> hc((size_t)ncod);
+    TRY(d2h(hc.data(), p->cod, ncod, s));
+    for (int k = 0; k < 3; ++k) p->ncod_type[k] = 0;
+    for (const dcod& c : hc) p->ncod_type[c.type]++;
+    fill_stats(p, hc);
+    std::vector<int32_t> hst((size_t)n + 1);
+    TRY(d2h(hst.data(), p->starts, (int64_t)n + 1, s));
+    ddf_plan_stats_t& S = p->stats;
+    int64_t sentries = 0, psc2_idx_rows = 0, perm_rows = 0;
+    for (const dcod& c : hc) {
+        int64_t pts = (int64_t)hst[c.q0 + c.m] - hst[c.q0];
+        S.ops[c.type] += pts;
+        if (c.type == DDF_PSC1) sentries += c.n;
+        if (c.type == DDF_PSC2) psc2_idx_rows += c.m + 1;
+        if (!(c.flags & DC_F_STRIDED)) perm_rows += c.m;
+    }
+    for (int32_t q = 0; q < n; ++q) S.max_row_len = std::max<int64_t>(S.max_row_len, hst[q + 1] - hst[q]);
+    int64_t desc = 64 * ncod;   // codelet descriptors (work units are a scheduling detail)
+    if (p->kind == DDF_SPMV) {
+        S.bytes_exec = 8 * S.points + 8 * (int64_t)p->n_cols + 8 * (int64_t)n + 4 * S.ops[DDF_PSC2] +
+                       4 * psc2_idx_rows + 4 * sentries + desc;
+    } else {
+        S.bytes_exec = 8 * S.points + 8 * (int64_t)n /*dinv*/ + 8 * (int64_t)n /*b*/ +
+                       16 * (int64_t)n /*x fill + write*/ + 4 * S.ops[DDF_PSC2] + 4 * psc2_idx_rows +
+                       4 * perm_rows + 4 * sentries + desc;
+    }
+    p->stats_ready = 1;
+    return DDF_OK;
+}
+
+// New values in the original CSR order, same pattern.
+ddf_status ddf_gather_values(ddf_plan_s* p, const double* values, cudaStream_t s) {
+    if (p->kind == DDF_SPMV) {
+        if (p->nnz > 0)
+            DDF_CUDA_TRY(cudaMemcpyAsync(p->val, values, (size_t)p->nnz * 8, cudaMemcpyDeviceToDevice, s));
+        p->has_values = 1;
+        return DDF_OK;
+    }
+    int32_t n = p->n;
+    if (n > 0) {
+        k_rel_gather<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, p->seq, p->orig_rowptr, nullptr, values,
+                                                    p->starts, nullptr, p->val, p->dinv);
+        ddf_count_launch();
+    }
+    DDF_CUDA_TRY(cudaGetLastError());
+    p->has_values = 1;
+    return DDF_OK;
+}

@@ -1,0 +1,160 @@
+// Internal declarations shared by the CUDA translation units of libddf.so.
+// Nothing here is part of the public ABI (include/ddf.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ddf.h"
+
+#define DDF_MAX_T 512          // largest mining window t (local mask of 512 bits)
+#define DDF_WARPS_PER_CTA 8
+#define DDF_CTA_THREADS (32 * DDF_WARPS_PER_CTA)
+
+// Executor codelet descriptor (64 bytes).  Access functions of the codelet's
+// rows i0 in [0, m) and points i1 in [0, n):
+//   f(i0)     = f0 + rho*i0            (F_STRIDED)   else seq[q0 + i0]
+//   g(i0, i1) = g0 + gamma*i0 + i1     (G_STRIDED)   else starts[q0 + i0] + i1
+//   h(i0, i1) = h0 + delta*i0 + sigma*i1              (BLAS)
+//             = h0 + delta*i0 + (col[sref + i1] - h0) (PSC I: s = first row's columns)
+//             = col[g(i0, i1)]                         (PSC II)
+struct dcod {
+    int32_t q0, m, n, type;
+    int32_t part, flags;
+    int32_t f0, rho;
+    int32_t g0, gamma;
+    int32_t h0, delta, sigma, sref;
+    int32_t pad0, pad1;
+};
+static_assert(sizeof(dcod) == 64, "dcod layout");
+
+enum { DC_F_STRIDED = 1, DC_G_STRIDED = 2 };
+
+// Executor work unit: rows [i0b, i0e) of codelet `cod`, processed by one warp
+// with `v` lanes per row (a power of two, 1..32).
+struct dunit {
+    int32_t cod, i0b, i0e, v;
+};
+static_assert(sizeof(dunit) == 16, "dunit layout");
+
+// The plan: every pointer is device memory owned by the plan.
+struct ddf_plan_s {
+    ddf_kind kind;
+    ddf_opts opts;
+    int device;
+    cudaStream_t stream;          // stream the plan was built on (used to free it)
+    int32_t n, n_cols, depth;
+    int64_t nnz;                  // entries of the inspected CSR
+    int64_t npts;                 // iteration points (SpTRSV: off-diagonal entries)
+    int has_values;
+    // executor layout ("sequence CSR"): positions q, starts[q] .. starts[q+1]
+    int32_t* starts;              // SpMV: CSR rowptr copy; SpTRSV: level-ordered off-diagonal starts
+    int32_t* col;                 // columns in that layout
+    double* val;                  // values in that layout
+    int32_t* seq;                 // SpTRSV: row at each position (level order); SpMV: NULL
+    int32_t* part_ptr;            // [depth + 1]
+    double* dinv;                 // SpTRSV: 1 / L_ii per position
+    int32_t* orig_rowptr;         // SpTRSV: rowptr of the inspected L (for ddf_update_values)
+    // codelets and units
+    dcod* cod;
+    int64_t ncod;
+    int64_t ncod_type[3];
+    dunit* units[3];              // SpMV: one list per type; SpTRSV: units[0] = all, level order
+    int64_t nunits[3];
+    // device scratch / status
+    int32_t* status;              // device status word (ddf_status)
+    uint32_t* ticket;             // SpTRSV: work ticket
+    int32_t last_launches;
+    int32_t units_per_cta;
+    int32_t sm_count;
+    // statistics, computed on the first ddf_plan_stats call
+    int32_t stats_ready;
+    ddf_plan_stats_t stats;
+};
+
+#define DDF_SENTINEL 0xFFFFFFFFFFFFFFFFull   // fill pattern of x during a solve (a NaN)
+#define DDF_CANON_NAN 0x7FF8000000000000ull
+
+#define DDF_CUDA_TRY(call)                         \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) {                   \
+            (void)cudaGetLastError();              \
+            return e_ == cudaErrorMemoryAllocation ? DDF_ERR_OOM : DDF_ERR_CUDA; \
+        }                                          \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// memory-model helpers (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ddf_ld_relaxed_u64(const void* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void ddf_st_relaxed_u64(void* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ int32_t ddf_ld_relaxed_s32(const void* p) {
+    int32_t v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void ddf_st_relaxed_s32(void* p, int32_t v) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ddf_globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void ddf_set_status(int32_t* status, int32_t code) {
+    atomicCAS(status, 0, code);
+}
+
+// ---------------------------------------------------------------------------
+// host-side launchers implemented in the .cu files
+// ---------------------------------------------------------------------------
+// ddf_scan.cu
+ddf_status ddf_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+ddf_status ddf_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+ddf_status ddf_radix_sort_u32(uint32_t* keys, int32_t* vals, int64_t n, uint32_t max_key,
+                              cudaStream_t s);
+// ddf_inspect.cu
+ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* colidx,
+                          const double* values, cudaStream_t s);
+ddf_status ddf_gather_values(ddf_plan_s* p, const double* values, cudaStream_t s);
+ddf_status ddf_compute_stats(ddf_plan_s* p);
+// ddf_spmv.cu
+ddf_status ddf_launch_spmv(ddf_plan_s* p, const double* x, double* y, cudaStream_t s);
+// ddf_sptrsv.cu
+ddf_status ddf_launch_sptrsv(ddf_plan_s* p, const double* b, double* x, cudaStream_t s);
+
+// process-wide count of kernel launches (ddf_capi.cu)
+void ddf_count_launch(int64_t k = 1);
+
+// device allocation helpers (stream-ordered)
+template <typename T>
+static inline ddf_status ddf_alloc(T** ptr, int64_t count, cudaStream_t s) {
+    *ptr = nullptr;
+    if (count <= 0) return DDF_OK;
+    cudaError_t e = cudaMallocAsync((void**)ptr, (size_t)count * sizeof(T), s);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        *ptr = nullptr;
+        return e == cudaErrorMemoryAllocation ? DDF_ERR_OOM : DDF_ERR_CUDA;
+    }
+    return DDF_OK;
+}
+template <typename T>
+static inline void ddf_free(T*& ptr, cudaStream_t s) {
+    if (ptr) (void)cudaFreeAsync((void*)ptr, s);
+    ptr = nullptr;
+}
+
+static inline unsigned ddf_grid(int64_t work, int per_block, unsigned cap = 0x7fffffffu) {
+    int64_t g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > (int64_t)cap) g = cap;
+    return (unsigned)g;
+}

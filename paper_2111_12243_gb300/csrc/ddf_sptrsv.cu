@@ -1,0 +1,179 @@
+// SpTRSV executor: forward substitution L x = b over the level-ordered plan.
+//
+// Partitions (levels) run in order and the codelets of one level together
+// (Sec. IV-A: partitions in sequence, codelets of a partition in parallel),
+// without a barrier between levels: every row waits only for the rows it
+// reads.  The ready flag of row j is x[j] itself: the call first fills x with
+// a NaN pattern that arithmetic never produces, and a row is ready once its
+// entry holds anything else.  One 64-bit load therefore both checks the flag
+// and fetches the value.
+//
+// Work units are ordered by level.  Each CTA takes the next chunk of units
+// from a ticket counter when it starts, so every unit it waits on belongs to
+// a CTA that already runs: waits always end.  Each wait is still bounded by
+// spin_cap_ns (globaltimer); when it runs out the kernel latches
+// DDF_ERR_TIMEOUT in the status word, stops waiting anywhere, and completes
+// with NaN in the rows concerned.
+#include "ddf_internal.cuh"
+
+namespace {
+
+constexpr int SMAX = 4;   // points per lane held in registers before the dependency reads
+
+__global__ void k_fill(unsigned long long* __restrict__ x, int64_t n, uint32_t* __restrict__ ticket) {
+    int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i0 == 0) {
+        ticket[0] = 0u;   // work ticket
+        ticket[1] = 0u;   // abort flag of this call
+    }
+    for (int64_t i = i0; i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] = DDF_SENTINEL;
+}
+
+// Bounded wait for x[j]: a few immediate polls, then exponential backoff
+// (32 ns doubling to 256 ns) so that waiting warps do not flood L2.
+__device__ __noinline__ double wait_x(const double* p, int32_t* status, uint32_t* abort_flag,
+                                      int64_t cap_ns) {
+    uint64_t t0 = ddf_globaltimer();
+    uint32_t it = 0, ns = 32;
+    while (true) {
+        unsigned long long v = ddf_ld_relaxed_u64(p);
+        if (v != DDF_SENTINEL) return __longlong_as_double((long long)v);
+        ++it;
+        if (it > 8) {
+            __nanosleep(ns);
+            ns = min(ns * 2, 256u);
+        }
+        if ((it & 15u) == 0) {
+            if (ddf_ld_relaxed_s32(abort_flag) != 0) return __longlong_as_double((long long)DDF_CANON_NAN);
+            if ((int64_t)(ddf_globaltimer() - t0) > cap_ns) {
+                ddf_set_status(status, DDF_ERR_TIMEOUT);
+                atomicExch(abort_flag, 1u);
+                return __longlong_as_double((long long)DDF_CANON_NAN);
+            }
+        }
+    }
+}
+
+// Read x[j] once it is ready (plain relaxed load first, bounded wait after).
+__device__ __forceinline__ double dep(const double* x, int32_t j, int32_t* status, uint32_t* abort_flag,
+                                      int64_t cap_ns) {
+    unsigned long long v = ddf_ld_relaxed_u64(x + j);
+    if (v != DDF_SENTINEL) return __longlong_as_double((long long)v);
+    return wait_x(x + j, status, abort_flag, cap_ns);
+}
+
+// One warp per work unit; a unit is the rows one warp pass covers (32 / v
+// rows, v lanes per row).  Everything that does not depend on x (descriptor,
+// row index, values, columns, b, 1/L_ii) is loaded before the first
+// dependency is read, and the reads of all dependencies of a lane are issued
+// together, so a unit waiting on an earlier level only pays the flag hop.
+__global__ void __launch_bounds__(DDF_CTA_THREADS)
+k_sptrsv(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64_t nunits, int32_t upc,
+         const int32_t* __restrict__ seq, const int32_t* __restrict__ st, const int32_t* __restrict__ col,
+         const double* __restrict__ val, const double* __restrict__ dinv, const double* __restrict__ b,
+         double* x, uint32_t* ticket, int32_t* status, int64_t cap_ns) {
+    __shared__ uint32_t chunk;
+    if (threadIdx.x == 0) chunk = atomicAdd(ticket, 1u);
+    __syncthreads();
+    uint32_t* abort_flag = ticket + 1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t ub = (int64_t)chunk * upc;
+    const int64_t ue = min(ub + (int64_t)upc, nunits);
+    for (int64_t u = ub + w; u < ue; u += DDF_WARPS_PER_CTA) {
+        const dunit U = units[u];
+        const dcod C = cod[U.cod];
+        const int v = U.v;
+        const int lg = __ffs(v) - 1;
+        const int rpw = 32 >> lg;
+        const int sub = lane >> lg;
+        const int li = lane & (v - 1);
+        for (int32_t ib = U.i0b; ib < U.i0e; ib += rpw) {
+            const int32_t i0 = ib + sub;
+            const bool act = i0 < U.i0e;
+            const int32_t q = C.q0 + i0;
+            int32_t r = 0, kb = 0, L = 0, hb = 0;
+            double bv = 0.0, di = 0.0;
+            double vv[SMAX];
+            int32_t jj[SMAX];
+#pragma unroll
+            for (int k = 0; k < SMAX; ++k) {
+                vv[k] = 0.0;
+                jj[k] = -1;
+            }
+            if (act) {
+                r = (C.flags & DC_F_STRIDED) ? C.f0 + C.rho * i0 : seq[q];
+                if (C.type == DDF_PSC2) {
+                    kb = st[q];
+                    L = st[q + 1] - kb;
+                } else {
+                    kb = C.g0 + C.gamma * i0;
+                    L = C.n;
+                }
+                hb = C.h0 + C.delta * i0;
+                bv = b[r];
+                di = dinv[q];
+#pragma unroll
+                for (int k = 0; k < SMAX; ++k) {
+                    const int32_t i1 = li + k * v;
+                    if (i1 < L) {
+                        vv[k] = val[kb + i1];
+                        jj[k] = (C.type == DDF_BLAS)   ? hb + C.sigma * i1
+                                : (C.type == DDF_PSC1) ? hb + (col[C.sref + i1] - C.h0)
+                                                       : col[kb + i1];
+                    }
+                }
+            }
+            double acc = 0.0;
+            if (act) {
+                unsigned long long xv[SMAX];
+#pragma unroll
+                for (int k = 0; k < SMAX; ++k) xv[k] = jj[k] >= 0 ? ddf_ld_relaxed_u64(x + jj[k]) : 0ull;
+#pragma unroll
+                for (int k = 0; k < SMAX; ++k) {
+                    if (jj[k] >= 0) {
+                        double xd = (xv[k] != DDF_SENTINEL) ? __longlong_as_double((long long)xv[k])
+                                                            : wait_x(x + jj[k], status, abort_flag, cap_ns);
+                        acc += vv[k] * xd;
+                    }
+                }
+                for (int32_t i1 = li + SMAX * v; i1 < L; i1 += v) {
+                    const int32_t j = (C.type == DDF_BLAS)   ? hb + C.sigma * i1
+                                      : (C.type == DDF_PSC1) ? hb + (col[C.sref + i1] - C.h0)
+                                                             : col[kb + i1];
+                    acc += val[kb + i1] * dep(x, j, status, abort_flag, cap_ns);
+                }
+            }
+            for (int o = v >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (act && li == 0) {
+                double xr = (bv - acc) * di;
+                unsigned long long bits = (unsigned long long)__double_as_longlong(xr);
+                if (bits == DDF_SENTINEL) bits = DDF_CANON_NAN;
+                ddf_st_relaxed_u64(x + r, bits);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+ddf_status ddf_launch_sptrsv(ddf_plan_s* p, const double* b, double* x, cudaStream_t s) {
+    int64_t n = p->n;
+    int sm = p->sm_count > 0 ? p->sm_count : 152;
+    k_fill<<<ddf_grid(n > 0 ? n : 1, 256, (unsigned)sm * 8), 256, 0, s>>>((unsigned long long*)x, n,
+                                                                          p->ticket);
+    ddf_count_launch();
+    int launches = 1;
+    int64_t nu = p->nunits[0];
+    if (nu > 0) {
+        int32_t upc = p->units_per_cta > 0 ? p->units_per_cta : DDF_WARPS_PER_CTA;
+        int64_t ctas = (nu + upc - 1) / upc;
+        k_sptrsv<<<(unsigned)ctas, DDF_CTA_THREADS, 0, s>>>(p->cod, p->units[0], nu, upc, p->seq, p->starts,
+                                                           p->col, p->val, p->dinv, b, x, p->ticket,
+                                                           p->status, p->opts.spin_cap_ns);
+        ddf_count_launch();
+        ++launches;
+    }
+    p->last_launches = launches;
+    DDF_CUDA_TRY(cudaGetLastError());
+    return DDF_OK;
+}

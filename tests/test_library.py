@@ -1,0 +1,78 @@
+"""Host-side checks of the C ABI library (no GPU compute).
+
+The library is built for sm_103a with nvcc (cross-compiles without a GPU),
+loaded through ctypes, and must export every function include/ddf.h declares.
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2111_12243_gb300 as ddf
+from paper_2111_12243_gb300 import build as ddf_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ddf.h")
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return ddf_build.build()
+
+
+def header_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^DDF_API\s+[\w\s\*]*?\b(ddf_\w+)\s*\(", text, re.M)))
+
+
+def test_header_declares_the_exports():
+    assert header_functions() == sorted(ddf.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r" T (ddf_\w+)$", out, re.M))
+    assert set(header_functions()) <= exported
+    # nothing else leaks out of the library under the ddf_ prefix
+    assert exported == set(header_functions())
+
+
+def test_library_loads_and_host_calls(libpath):
+    L = ddf.lib()
+    for name in ddf.EXPORTS:
+        assert hasattr(L, name)
+    o = ddf.ddf_opts_default()
+    assert (o.window_t, o.allowed_types, o.w_op, o.w_codelet, o.w_index, o.unit_nnz) == (
+        256, 7, 8, 32, 4, 256)
+    assert ddf.ddf_status_string(0) == "ok"
+    assert "timed out" in ddf.ddf_status_string(11)
+    assert ddf.ddf_status_string(999) == "unknown status"
+
+
+def test_ctypes_layouts_match_header():
+    # ddf_csr: 2 x int32, int64, 3 pointers, 2 x int32
+    assert ctypes.sizeof(ddf.ddf_csr) == 4 + 4 + 8 + 3 * 8 + 4 + 4
+    assert ctypes.sizeof(ddf.ddf_opts) == 2 * 4 + 4 * 8 + 4 + 9 * 4
+    assert ctypes.sizeof(ddf.ddf_plan_stats_t) == 4 * 4 + 8 * (2 + 9 + 3 + 6)
+
+
+def test_host_argument_errors_without_gpu(libpath):
+    # NULL output handle and bad kinds fail before any CUDA call
+    L = ddf.lib()
+    A = ddf.ddf_csr()
+    assert L.ddf_inspect(ctypes.byref(A), 1, None, None, None) == 1
+    h = ctypes.c_void_p()
+    assert L.ddf_inspect(ctypes.byref(A), 3, None, None, ctypes.byref(h)) == 1
+    A.n_rows, A.n_cols = 3, 4
+    A.rowptr = ctypes.c_void_p(1)
+    assert L.ddf_inspect(ctypes.byref(A), 2, None, None, ctypes.byref(h)) == 2   # not square
+    o = ddf.ddf_opts_default(window_t=0)
+    assert L.ddf_inspect(ctypes.byref(A), 1, ctypes.byref(o), None, ctypes.byref(h)) == 1
+    o = ddf.ddf_opts_default(allowed_types=ddf.DDF_ALLOW_BLAS)
+    assert L.ddf_inspect(ctypes.byref(A), 1, ctypes.byref(o), None, ctypes.byref(h)) == 1
+    assert L.ddf_spmv(None, None, None, None) == 1
+    assert L.ddf_sptrsv(None, None, None, None) == 1
+    assert L.ddf_last_launches(None) == 0
