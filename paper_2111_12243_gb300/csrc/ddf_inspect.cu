@@ -296,188 +296,271 @@ __global__ void k_features(int32_t n, const int32_t* __restrict__ seq, const int
 }
 
 // ---------------------------------------------------------------------------
-// mining strategies (one thread per region)
+// mining strategies (one warp per region)
+//
+// The warp first turns the region's FOPD features into 512-bit predicate
+// masks over the local positions i = q - a (one ballot per 32 positions):
+//   hstr   row i has evenly spaced columns (Delta_i1 h constant)
+//   ok     link (i-1, i): equal lengths and a translated pattern
+//   same   ok at i and i-1 with the same strides (Delta_i0 of f, g, h)
+//   chF    Delta_i0 f changes at i        chG  Delta_i0 g changes at i
+//   neq    rows i-1 and i differ in length
+// The three greedy strategies then run on lane 0 as bit scans over these
+// masks: each step jumps to the next candidate position, so a region costs
+// O(pieces) instead of O(t) per strategy.  The decisions are the same as
+// the position-by-position definition (and as the oracle's).
 // ---------------------------------------------------------------------------
 struct Weights {
     int64_t op, cl, idx;
 };
 
-__device__ __forceinline__ int32_t ext_psc1(const Feat& F, int32_t q0, int32_t end) {
-    int32_t q1 = q0 + 1;
-    if (q1 >= end) return q1;
-    uint8_t f = F.fl[q1];
-    if (!(f & FL_EQLEN) || !(f & FL_TRANS)) return q1;
-    int32_t rf = F.dF[q1], rg = F.dG[q1], rh = F.dH[q1];
-    ++q1;
-    while (q1 < end) {
-        f = F.fl[q1];
-        if (!(f & FL_EQLEN) || !(f & FL_TRANS) || F.dF[q1] != rf || F.dG[q1] != rg || F.dH[q1] != rh)
-            break;
-        ++q1;
+constexpr int MW = DDF_MAX_T / 32;    // 32-bit words per region mask
+constexpr int MINE_WARPS = 4;
+
+struct RegionMasks {
+    uint32_t hstr[MW], ok[MW], same[MW], chF[MW], chG[MW], neq[MW], cov[MW];
+    int32_t st[DDF_MAX_T + 1];        // starts[a + i] - starts[a]
+};
+
+// smallest j in [from, end) whose bit equals `want`, else end
+__device__ __forceinline__ int32_t next_bit(const uint32_t* m, int32_t from, int32_t end, bool want) {
+    if (from >= end) return end;
+    int32_t w = from >> 5;
+    uint32_t word = want ? m[w] : ~m[w];
+    word &= ~0u << (from & 31);
+    const int32_t wl = (end - 1) >> 5;
+    while (true) {
+        if (word) {
+            int32_t pos = (w << 5) + __ffs(word) - 1;
+            return pos < end ? pos : end;
+        }
+        if (++w > wl) return end;
+        word = want ? m[w] : ~m[w];
     }
-    return q1;
 }
 
-__device__ __forceinline__ bool run_F(const Feat& F, int32_t q0, int32_t q1) {
-    for (int32_t q = q0 + 2; q < q1; ++q)
-        if (F.dF[q] != F.dF[q0 + 1]) return false;
-    return true;
+__device__ __forceinline__ bool any_bit(const uint32_t* m, int32_t from, int32_t end) {
+    return next_bit(m, from, end, true) < end;
 }
 
-__device__ __forceinline__ bool run_G(const Feat& F, int32_t q0, int32_t q1) {
-    for (int32_t q = q0 + 1; q < q1; ++q)
-        if (!(F.fl[q] & FL_EQLEN) || F.dG[q] != F.dG[q0 + 1]) return false;
-    return true;
+__device__ __forceinline__ void set_bits(uint32_t* m, int32_t from, int32_t end) {
+    for (int32_t i = from; i < end;) {
+        int32_t w = i >> 5, b = i & 31;
+        int32_t k = min(32 - b, end - i);
+        uint32_t bits = (k == 32) ? ~0u : (((1u << k) - 1u) << b);
+        m[w] |= bits;
+        i += k;
+    }
+}
+
+// maximal run from i with f, g strided and a shared s (PSC I form)
+__device__ __forceinline__ int32_t ext_run(const RegionMasks& R, int32_t i, int32_t end) {
+    int32_t i1 = i + 1;
+    if (i1 >= end || !((R.ok[i1 >> 5] >> (i1 & 31)) & 1u)) return i1;
+    return next_bit(R.same, i + 2, end, false);
+}
+
+__device__ __forceinline__ bool run_F(const RegionMasks& R, int32_t i, int32_t j) {
+    return !any_bit(R.chF, i + 2, j);
+}
+__device__ __forceinline__ bool run_G(const RegionMasks& R, int32_t i, int32_t j) {
+    return !any_bit(R.neq, i + 1, j) && !any_bit(R.chG, i + 2, j);
 }
 
 // Eq. 1: c = w_op |p| + w_cl + w_idx (|s_f| + |s_g| + |s_h|)
-__device__ int64_t piece_cost(const Feat& F, int type, int32_t q0, int32_t q1, const Weights& w) {
-    int64_t m = q1 - q0;
-    int64_t p = (int64_t)F.st[q1] - F.st[q0];
+__device__ int64_t piece_cost(const RegionMasks& R, int type, int32_t i, int32_t j, const Weights& w) {
+    int64_t m = j - i;
+    int64_t p = (int64_t)R.st[j] - R.st[i];
     int64_t sf = 0, sg = 0, sh = 0;
-    if (type == DDF_PSC1) sh = F.st[q0 + 1] - F.st[q0];
+    if (type == DDF_PSC1) sh = R.st[i + 1] - R.st[i];
     if (type == DDF_PSC2) {
-        sf = run_F(F, q0, q1) ? 0 : m;
-        sg = run_G(F, q0, q1) ? 0 : m;
+        sf = run_F(R, i, j) ? 0 : m;
+        sg = run_G(R, i, j) ? 0 : m;
         sh = p;
     }
     return w.op * p + w.cl + w.idx * (sf + sg + sh);
 }
 
-struct Cov {
-    uint32_t b[DDF_MAX_T / 32];
-    __device__ void clear(int32_t len) {
-        for (int i = 0; i < (len + 31) / 32; ++i) b[i] = 0;
-    }
-    __device__ bool get(int32_t i) const { return (b[i >> 5] >> (i & 31)) & 1u; }
-    __device__ void set(int32_t i0, int32_t i1) {
-        for (int32_t i = i0; i < i1; ++i) b[i >> 5] |= 1u << (i & 31);
-    }
-};
-
 struct Sink {
-    int8_t* mark;   // NULL: cost only
+    const RegionMasks* R;
+    int8_t* mark;       // global marks of the region (NULL: cost only)
+    int32_t* plen;
+    int32_t* lidx;
     int64_t cost;
     int32_t pieces;
-    __device__ void put(const Feat& F, int type, int32_t q0, int32_t q1, const Weights& w) {
-        cost += piece_cost(F, type, q0, q1, w);
+    __device__ void put(int type, int32_t i, int32_t j, const Weights& w) {
+        cost += piece_cost(*R, type, i, j, w);
+        if (mark) {
+            int flags = (run_F(*R, i, j) ? 4 : 0) | (run_G(*R, i, j) ? 8 : 0);
+            mark[i] = (int8_t)(type | flags);
+            plen[i] = j - i;
+            lidx[i] = pieces;
+        }
         ++pieces;
-        if (mark) mark[q0] = (int8_t)type;
     }
 };
 
-__device__ void leftovers(const Feat& F, const Cov& cov, int32_t a, int32_t b, const Weights& w,
-                          Sink& out) {
-    int32_t q = a;
-    while (q < b) {
-        if (cov.get(q - a)) { ++q; continue; }
-        int32_t u = q;
-        while (q < b && !cov.get(q - a)) ++q;
-        out.put(F, DDF_PSC2, u, q, w);
+__device__ void leftovers(const RegionMasks& R, int32_t len, const Weights& w, Sink& out) {
+    int32_t q = next_bit(R.cov, 0, len, false);
+    while (q < len) {
+        int32_t e = next_bit(R.cov, q, len, true);
+        out.put(DDF_PSC2, q, e, w);
+        q = next_bit(R.cov, e, len, false);
     }
 }
 
-__device__ void blas_first(const Feat& F, int32_t a, int32_t b, int allowed, const Weights& w,
-                           Cov& cov, Sink& out) {
-    cov.clear(b - a);
-    int32_t q = a;
-    while (q < b) {
-        if (F.fl[q] & FL_HSTR) {
-            int32_t q1 = ext_psc1(F, q, b);
-            out.put(F, DDF_BLAS, q, q1, w);
-            cov.set(q - a, q1 - a);
-            q = q1;
-        } else {
-            ++q;
-        }
+__device__ void clear_cov(RegionMasks& R) {
+    for (int k = 0; k < MW; ++k) R.cov[k] = 0u;
+}
+
+__device__ void blas_first(RegionMasks& R, int32_t len, int allowed, const Weights& w, Sink& out) {
+    clear_cov(R);
+    int32_t q = next_bit(R.hstr, 0, len, true);            // maximal BLAS runs
+    while (q < len) {
+        int32_t q1 = ext_run(R, q, len);
+        out.put(DDF_BLAS, q, q1, w);
+        set_bits(R.cov, q, q1);
+        q = next_bit(R.hstr, q1, len, true);
     }
-    if (allowed & DDF_ALLOW_PSC1) {
-        q = a;
-        while (q < b) {
-            if (cov.get(q - a)) { ++q; continue; }
-            int32_t v = q;
-            while (v < b && !cov.get(v - a)) ++v;
+    if (allowed & DDF_ALLOW_PSC1) {                        // PSC I runs in the gaps
+        q = next_bit(R.cov, 0, len, false);
+        while (q < len) {
+            const int32_t v = next_bit(R.cov, q, len, true);
             int32_t u = q;
             while (u < v) {
-                int32_t u1 = ext_psc1(F, u, v);
+                int32_t u1 = ext_run(R, u, v);
                 if (u1 - u >= 2) {
-                    out.put(F, DDF_PSC1, u, u1, w);
-                    cov.set(u - a, u1 - a);
+                    out.put(DDF_PSC1, u, u1, w);
+                    set_bits(R.cov, u, u1);
                     u = u1;
                 } else {
-                    ++u;
+                    // next start that can extend: ok at its successor
+                    int32_t nx = next_bit(R.ok, u + 2, v, true);
+                    u = (nx < v) ? nx - 1 : v;
                 }
             }
-            q = v;
+            q = next_bit(R.cov, v, len, false);
         }
     }
-    leftovers(F, cov, a, b, w, out);
+    leftovers(R, len, w, out);
 }
 
-__device__ void psc1_first(const Feat& F, int32_t a, int32_t b, int allowed, const Weights& w,
-                           Cov& cov, Sink& out) {
-    cov.clear(b - a);
-    int32_t q = a;
-    while (q < b) {
-        int32_t q1 = ext_psc1(F, q, b);
+__device__ void psc1_first(RegionMasks& R, int32_t len, int allowed, const Weights& w, Sink& out) {
+    clear_cov(R);
+    int32_t q = 0;
+    while (q < len) {
+        int32_t q1 = ext_run(R, q, len);
         if (q1 - q >= 2) {
-            int t = ((F.fl[q] & FL_HSTR) && (allowed & DDF_ALLOW_BLAS)) ? DDF_BLAS : DDF_PSC1;
-            out.put(F, t, q, q1, w);
-            cov.set(q - a, q1 - a);
+            bool h = (R.hstr[q >> 5] >> (q & 31)) & 1u;
+            out.put((h && (allowed & DDF_ALLOW_BLAS)) ? DDF_BLAS : DDF_PSC1, q, q1, w);
+            set_bits(R.cov, q, q1);
             q = q1;
         } else {
-            ++q;
+            int32_t nx = next_bit(R.ok, q + 2, len, true);
+            q = (nx < len) ? nx - 1 : len;
         }
     }
-    leftovers(F, cov, a, b, w, out);
+    leftovers(R, len, w, out);
 }
 
-// Pass 1: choose the strategy of least total cost (ties: BLAS_first, then
-// PSCI_first), write its piece starts into `mark` and the piece count.
-__global__ void k_mine(int64_t nreg, const int32_t* __restrict__ ra, const int32_t* __restrict__ rb,
-                       Feat F, int allowed, Weights w, int8_t* __restrict__ mark,
-                       int32_t* __restrict__ cnt) {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Pass 1: build the masks, choose the strategy of least total cost (ties:
+// BLAS_first, then PSCI_first), and record its pieces at their first
+// position: mark (type | F << 2 | G << 3), plen (rows) and lidx (index of the
+// piece inside the region).
+__global__ void __launch_bounds__(32 * MINE_WARPS)
+k_mine(int64_t nreg, const int32_t* __restrict__ ra, const int32_t* __restrict__ rb, Feat F, int allowed,
+       Weights w, int8_t* __restrict__ mark, int32_t* __restrict__ plen, int32_t* __restrict__ lidx,
+       int32_t* __restrict__ cnt) {
+    __shared__ RegionMasks RM[MINE_WARPS];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * MINE_WARPS + wi;
     if (r >= nreg) return;
-    int32_t a = ra[r], b = rb[r];
-    Cov cov;
-    int64_t C[3];
-    int best = -1;
-    for (int s = 0; s < 3; ++s) {
-        if (s == 0 && !(allowed & DDF_ALLOW_BLAS)) continue;
-        if (s == 1 && !(allowed & DDF_ALLOW_PSC1)) continue;
-        Sink k{nullptr, 0, 0};
-        if (s == 0) blas_first(F, a, b, allowed, w, cov, k);
-        else if (s == 1) psc1_first(F, a, b, allowed, w, cov, k);
-        else k.put(F, DDF_PSC2, a, b, w);
-        C[s] = k.cost;
-        if (best < 0 || C[s] < C[best]) best = s;
+    RegionMasks& R = RM[wi];
+    const int32_t a = ra[r], len = rb[r] - a;
+    const int32_t s0 = F.st[a];
+    int32_t pdF = 0, pdG = 0, pdH = 0;
+    bool pok = false;
+    for (int32_t c = 0; c * 32 < len; ++c) {
+        const int32_t i = c * 32 + lane;
+        const bool valid = i < len;
+        const int64_t q = (int64_t)a + i;
+        uint8_t f = valid ? F.fl[q] : 0;
+        int32_t df = valid ? F.dF[q] : 0, dg = valid ? F.dG[q] : 0, dh = valid ? F.dH[q] : 0;
+        // values of position i - 1 (lane 0 takes them from the previous chunk)
+        int32_t udF = __shfl_up_sync(0xffffffffu, df, 1);
+        int32_t udG = __shfl_up_sync(0xffffffffu, dg, 1);
+        int32_t udH = __shfl_up_sync(0xffffffffu, dh, 1);
+        bool ok = valid && i >= 1 && (f & FL_EQLEN) && (f & FL_TRANS);
+        bool uok = __shfl_up_sync(0xffffffffu, ok, 1);
+        if (lane == 0) {
+            udF = pdF;
+            udG = pdG;
+            udH = pdH;
+            uok = pok;
+        }
+        bool same = ok && i >= 2 && uok && df == udF && dg == udG && dh == udH;
+        uint32_t bh = __ballot_sync(0xffffffffu, valid && (f & FL_HSTR));
+        uint32_t bo = __ballot_sync(0xffffffffu, ok);
+        uint32_t bs = __ballot_sync(0xffffffffu, same);
+        uint32_t bf = __ballot_sync(0xffffffffu, valid && i >= 2 && df != udF);
+        uint32_t bg = __ballot_sync(0xffffffffu, valid && i >= 2 && dg != udG);
+        uint32_t bn = __ballot_sync(0xffffffffu, valid && i >= 1 && !(f & FL_EQLEN));
+        if (lane == 0) {
+            R.hstr[c] = bh;
+            R.ok[c] = bo;
+            R.same[c] = bs;
+            R.chF[c] = bf;
+            R.chG[c] = bg;
+            R.neq[c] = bn;
+        }
+        pdF = __shfl_sync(0xffffffffu, df, 31);
+        pdG = __shfl_sync(0xffffffffu, dg, 31);
+        pdH = __shfl_sync(0xffffffffu, dh, 31);
+        pok = __shfl_sync(0xffffffffu, ok, 31);
     }
-    for (int32_t q = a; q < b; ++q) mark[q] = (int8_t)MK_NONE;
-    Sink k{mark, 0, 0};
-    if (best == 0) blas_first(F, a, b, allowed, w, cov, k);
-    else if (best == 1) psc1_first(F, a, b, allowed, w, cov, k);
-    else k.put(F, DDF_PSC2, a, b, w);
-    cnt[r] = k.pieces;
+    for (int32_t i = lane; i <= len; i += 32) R.st[i] = F.st[a + i] - s0;
+    for (int32_t i = lane; i < len; i += 32) mark[a + i] = (int8_t)MK_NONE;
+    __syncwarp();
+    if (lane == 0) {
+        int64_t C[3];
+        int best = -1;
+        for (int st = 0; st < 3; ++st) {
+            if (st == 0 && !(allowed & DDF_ALLOW_BLAS)) continue;
+            if (st == 1 && !(allowed & DDF_ALLOW_PSC1)) continue;
+            Sink k{&R, nullptr, nullptr, nullptr, 0, 0};
+            if (st == 0) blas_first(R, len, allowed, w, k);
+            else if (st == 1) psc1_first(R, len, allowed, w, k);
+            else k.put(DDF_PSC2, 0, len, w);
+            C[st] = k.cost;
+            if (best < 0 || C[st] < C[best]) best = st;
+        }
+        Sink k{&R, mark + a, plen + a, lidx + a, 0, 0};
+        if (best == 0) blas_first(R, len, allowed, w, k);
+        else if (best == 1) psc1_first(R, len, allowed, w, k);
+        else k.put(DDF_PSC2, 0, len, w);
+        cnt[r] = k.pieces;
+    }
 }
 
-// Pass 2 (cList.append): write the codelets of every region at its offset.
-__global__ void k_emit(int64_t nreg, const int32_t* __restrict__ ra, const int32_t* __restrict__ rb,
-                       const int32_t* __restrict__ rpart, Feat F, const int32_t* __restrict__ seq,
-                       const int32_t* __restrict__ col, const int8_t* __restrict__ mark,
-                       const int64_t* __restrict__ off, dcod* __restrict__ out) {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Pass 2 (cList.append): the lanes of a warp walk the region's positions and
+// write the codelet of every piece start at off[region] + its local index.
+__global__ void __launch_bounds__(32 * MINE_WARPS)
+k_emit(int64_t nreg, const int32_t* __restrict__ ra, const int32_t* __restrict__ rb,
+       const int32_t* __restrict__ rpart, Feat F, const int32_t* __restrict__ seq,
+       const int32_t* __restrict__ col, const int8_t* __restrict__ mark, const int32_t* __restrict__ plen,
+       const int32_t* __restrict__ lidx, const int64_t* __restrict__ off, dcod* __restrict__ out) {
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * MINE_WARPS + wi;
     if (r >= nreg) return;
-    int32_t a = ra[r], b = rb[r];
-    int64_t o = off[r];
-    int32_t q = a;
-    while (q < b) {
-        int type = mark[q];
-        int32_t e = q + 1;
-        while (e < b && mark[e] == MK_NONE) ++e;
-        int32_t m = e - q;
-        int32_t L = F.st[q + 1] - F.st[q];
-        bool fs = run_F(F, q, e), gs = run_G(F, q, e);
+    const int32_t a = ra[r], b = rb[r];
+    const int64_t o = off[r];
+    for (int32_t q = a + lane; q < b; q += 32) {
+        const int mk = mark[q];
+        if (mk == MK_NONE) continue;
+        const int type = mk & 3;
+        const bool fs = (mk & 4) != 0, gs = (mk & 8) != 0;
+        const int32_t m = plen[q];
+        const int32_t L = F.st[q + 1] - F.st[q];
         dcod c;
         c.q0 = q;
         c.m = m;
@@ -494,8 +577,7 @@ __global__ void k_emit(int64_t nreg, const int32_t* __restrict__ ra, const int32
         c.sigma = (type == DDF_BLAS && L >= 2) ? F.sig[q] : 0;
         c.sref = F.st[q];
         c.pad0 = c.pad1 = 0;
-        out[o++] = c;
-        q = e;
+        out[o + lidx[q]] = c;
     }
 }
 
@@ -799,13 +881,17 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
 
     // mining and append
     int8_t* mark = nullptr;
+    int32_t *plen = nullptr, *lidx = nullptr;
     int32_t* cnt = nullptr;
     int64_t* off = nullptr;
     TRY(tmp.get(&mark, n));
+    TRY(tmp.get(&plen, n));
+    TRY(tmp.get(&lidx, n));
     TRY(tmp.get(&cnt, nreg));
     TRY(tmp.get(&off, nreg + 1));
     if (nreg > 0) {
-        k_mine<<<ddf_grid(nreg, 64), 64, 0, s>>>(nreg, ra, rb, F, p->opts.allowed_types, w, mark, cnt);
+        k_mine<<<ddf_grid(nreg, MINE_WARPS), 32 * MINE_WARPS, 0, s>>>(nreg, ra, rb, F, p->opts.allowed_types, w,
+                                                                    mark, plen, lidx, cnt);
         ddf_count_launch();
     }
     DDF_CUDA_TRY(cudaGetLastError());
@@ -815,7 +901,8 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
     p->ncod = ncod;
     TRY(ddf_alloc(&p->cod, ncod, s));
     if (nreg > 0) {
-        k_emit<<<ddf_grid(nreg, 64), 64, 0, s>>>(nreg, ra, rb, rpart, F, seq, p->col, mark, off, p->cod);
+        k_emit<<<ddf_grid(nreg, MINE_WARPS), 32 * MINE_WARPS, 0, s>>>(nreg, ra, rb, rpart, F, seq, p->col, mark,
+                                                                    plen, lidx, off, p->cod);
         ddf_count_launch();
     }
     DDF_CUDA_TRY(cudaGetLastError());
