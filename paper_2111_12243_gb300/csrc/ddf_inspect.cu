@@ -146,10 +146,17 @@ k_levels(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t base = (int64_t)chunk * LEV_CHUNK;
     int32_t mymax = 0;
+    // row extents of the warp's LEV_RPW rows, one coalesced load per lane
+    const int64_t r0 = base + (int64_t)w * LEV_RPW;
+    int32_t ra_l = 0, rb_l = 0;
+    if (r0 + lane < n) {
+        ra_l = rp[r0 + lane];
+        rb_l = rp[r0 + lane + 1] - 1;   // the diagonal is last: not a dependency
+    }
     for (int rr = 0; rr < LEV_RPW; ++rr) {
-        const int64_t r = base + (int64_t)w * LEV_RPW + rr;
+        const int64_t r = r0 + rr;
         if (r >= n) break;
-        const int32_t a = rp[r], b = rp[r + 1] - 1;   // the diagonal is last: not a dependency
+        const int32_t a = __shfl_sync(0xffffffffu, ra_l, rr), b = __shfl_sync(0xffffffffu, rb_l, rr);
         int32_t m = -1;
         for (int32_t k = a + lane; k < b; k += 32) {
             const int32_t j = ci[k];
@@ -385,7 +392,6 @@ struct Sink {
     const RegionMasks* R;
     int8_t* mark;       // global marks of the region (NULL: cost only)
     int32_t* plen;
-    int32_t* lidx;
     int64_t cost;
     int32_t pieces;
     __device__ void put(int type, int32_t i, int32_t j, const Weights& w) {
@@ -394,7 +400,6 @@ struct Sink {
             int flags = (run_F(*R, i, j) ? 4 : 0) | (run_G(*R, i, j) ? 8 : 0);
             mark[i] = (int8_t)(type | flags);
             plen[i] = j - i;
-            lidx[i] = pieces;
         }
         ++pieces;
     }
@@ -527,18 +532,29 @@ k_mine(int64_t nreg, const int32_t* __restrict__ ra, const int32_t* __restrict__
         for (int st = 0; st < 3; ++st) {
             if (st == 0 && !(allowed & DDF_ALLOW_BLAS)) continue;
             if (st == 1 && !(allowed & DDF_ALLOW_PSC1)) continue;
-            Sink k{&R, nullptr, nullptr, nullptr, 0, 0};
+            Sink k{&R, nullptr, nullptr, 0, 0};
             if (st == 0) blas_first(R, len, allowed, w, k);
             else if (st == 1) psc1_first(R, len, allowed, w, k);
             else k.put(DDF_PSC2, 0, len, w);
             C[st] = k.cost;
             if (best < 0 || C[st] < C[best]) best = st;
         }
-        Sink k{&R, mark + a, plen + a, lidx + a, 0, 0};
+        Sink k{&R, mark + a, plen + a, 0, 0};
         if (best == 0) blas_first(R, len, allowed, w, k);
         else if (best == 1) psc1_first(R, len, allowed, w, k);
         else k.put(DDF_PSC2, 0, len, w);
         cnt[r] = k.pieces;
+    }
+    __syncwarp();
+    // codelets are appended in position order: the local index of a piece is
+    // the number of piece starts before it in the region
+    int32_t before = 0;
+    for (int32_t c = 0; c * 32 < len; ++c) {
+        const int32_t i = c * 32 + lane;
+        const bool start = i < len && mark[a + i] != (int8_t)MK_NONE;
+        const uint32_t bal = __ballot_sync(0xffffffffu, start);
+        if (start) lidx[a + i] = before + __popc(bal & ((1u << lane) - 1u));
+        before += __popc(bal);
     }
 }
 

@@ -8,12 +8,14 @@
 // entry holds anything else.  One 64-bit load therefore both checks the flag
 // and fetches the value.
 //
-// Work units are ordered by level.  Each CTA takes the next chunk of units
-// from a ticket counter when it starts, so every unit it waits on belongs to
-// a CTA that already runs: waits always end.  Each wait is still bounded by
-// spin_cap_ns (globaltimer); when it runs out the kernel latches
-// DDF_ERR_TIMEOUT in the status word, stops waiting anywhere, and completes
-// with NaN in the rows concerned.
+// Work units are ordered by level.  The solve is one persistent cooperative
+// launch: warp gw of W co-resident warps runs units gw, gw + W, gw + 2W, ...
+// in increasing order.  A unit waits only on units of earlier levels, which
+// have smaller indices; by induction on the unit index every wait ends,
+// because all W warps are resident (cooperative launch) and each runs its
+// units in order.  Each wait is still bounded by spin_cap_ns (globaltimer);
+// when it runs out the kernel latches DDF_ERR_TIMEOUT in the status word,
+// stops waiting anywhere, and completes with NaN in the rows concerned.
 #include "ddf_internal.cuh"
 
 namespace {
@@ -39,9 +41,9 @@ __device__ __noinline__ double wait_x(const double* p, int32_t* status, uint32_t
         unsigned long long v = ddf_ld_relaxed_u64(p);
         if (v != DDF_SENTINEL) return __longlong_as_double((long long)v);
         ++it;
-        if (it > 8) {
+        if (it > 32) {
             __nanosleep(ns);
-            ns = min(ns * 2, 256u);
+            ns = min(ns * 2, 128u);
         }
         if ((it & 15u) == 0) {
             if (ddf_ld_relaxed_s32(abort_flag) != 0) return __longlong_as_double((long long)DDF_CANON_NAN);
@@ -67,19 +69,15 @@ __device__ __forceinline__ double dep(const double* x, int32_t j, int32_t* statu
 // row index, values, columns, b, 1/L_ii) is loaded before the first
 // dependency is read, and the reads of all dependencies of a lane are issued
 // together, so a unit waiting on an earlier level only pays the flag hop.
-__global__ void __launch_bounds__(DDF_CTA_THREADS)
-k_sptrsv(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64_t nunits, int32_t upc,
+__global__ void __launch_bounds__(DDF_CTA_THREADS, 4)
+k_sptrsv(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64_t nunits,
          const int32_t* __restrict__ seq, const int32_t* __restrict__ st, const int32_t* __restrict__ col,
          const double* __restrict__ val, const double* __restrict__ dinv, const double* __restrict__ b,
          double* x, uint32_t* ticket, int32_t* status, int64_t cap_ns) {
-    __shared__ uint32_t chunk;
-    if (threadIdx.x == 0) chunk = atomicAdd(ticket, 1u);
-    __syncthreads();
     uint32_t* abort_flag = ticket + 1;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t ub = (int64_t)chunk * upc;
-    const int64_t ue = min(ub + (int64_t)upc, nunits);
-    for (int64_t u = ub + w; u < ue; u += DDF_WARPS_PER_CTA) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nunits; u += nw) {
         const dunit U = units[u];
         const dcod C = cod[U.cod];
         const int v = U.v;
@@ -165,11 +163,26 @@ ddf_status ddf_launch_sptrsv(ddf_plan_s* p, const double* b, double* x, cudaStre
     int launches = 1;
     int64_t nu = p->nunits[0];
     if (nu > 0) {
-        int32_t upc = p->units_per_cta > 0 ? p->units_per_cta : DDF_WARPS_PER_CTA;
-        int64_t ctas = (nu + upc - 1) / upc;
-        k_sptrsv<<<(unsigned)ctas, DDF_CTA_THREADS, 0, s>>>(p->cod, p->units[0], nu, upc, p->seq, p->starts,
-                                                           p->col, p->val, p->dinv, b, x, p->ticket,
-                                                           p->status, p->opts.spin_cap_ns);
+        int per_sm = 0;
+        DDF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sptrsv, DDF_CTA_THREADS, 0));
+        if (per_sm < 1) per_sm = 1;
+        int64_t ctas = (nu + DDF_WARPS_PER_CTA - 1) / DDF_WARPS_PER_CTA;
+        if (ctas > (int64_t)per_sm * sm) ctas = (int64_t)per_sm * sm;
+        const dcod* a_cod = p->cod;
+        const dunit* a_units = p->units[0];
+        const int32_t* a_seq = p->seq;
+        const int32_t* a_st = p->starts;
+        const int32_t* a_col = p->col;
+        const double* a_val = p->val;
+        const double* a_dinv = p->dinv;
+        uint32_t* a_ticket = p->ticket;
+        int32_t* a_status = p->status;
+        int64_t a_cap = p->opts.spin_cap_ns;
+        void* args[] = {(void*)&a_cod, (void*)&a_units, (void*)&nu, (void*)&a_seq, (void*)&a_st, (void*)&a_col,
+                        (void*)&a_val, (void*)&a_dinv, (void*)&b, (void*)&x, (void*)&a_ticket, (void*)&a_status,
+                        (void*)&a_cap};
+        DDF_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_sptrsv, dim3((unsigned)ctas),
+                                                 dim3(DDF_CTA_THREADS), args, 0, s));
         ddf_count_launch();
         ++launches;
     }
