@@ -203,6 +203,40 @@ DDF_API int64_t ddf_kernel_launches(void);
  */
 DDF_API ddf_status ddf_debug_set_dependency(ddf_plan_t p, int64_t k, int32_t col);
 
+/*
+ * Lower-triangular solve that allocates nothing (this entry point has no
+ * counterpart in the paper; it serves callers of this library that must not
+ * allocate device memory: code running inside a memory-pool or allocator
+ * hook, where calling cudaMalloc would re-enter the allocator; services with
+ * a fixed device-memory budget; and latency-critical loops that cannot afford
+ * the device-wide synchronisation cudaMalloc and cudaFree may imply).
+ *
+ * Solves L x = b by forward substitution directly on the caller's CSR lower
+ * triangle (device pointers: rowptr [n+1], colidx [nnz], values [nnz], b and x
+ * [n]; columns increasing, the diagonal last in each row), without a plan.
+ * Its scratch (a work ticket, a status word and one ready flag per row) lives
+ * in a file-scope device array of DDF_NOALLOC_MAX_ROWS + 64 words (4 MiB)
+ * that every GPU which loads the library holds until the process exits.
+ * n > DDF_NOALLOC_MAX_ROWS returns DDF_ERR_TOO_LARGE before any device work.
+ *
+ * The first call on a device looks up the device address of that array
+ * (cudaGetSymbolAddress, with the device current); make that first call
+ * before any stream capture.  Every call shares the array: its header is
+ * cleared at the start of each call, and rows are flagged with a per-call
+ * number, so stale flags of earlier calls are never mistaken for new ones;
+ * calls that overlap on the GPU (two streams, two threads) race and must not
+ * be issued.  The call synchronises stream s and returns the solve's status:
+ * DDF_ERR_MISSING_DIAG / DDF_ERR_NOT_LOWER / DDF_ERR_ZERO_DIAG for a
+ * malformed row (detected on the device; such rows are skipped, never read
+ * out of bounds), DDF_ERR_TIMEOUT when a dependency wait exceeds
+ * spin_cap_ns (nanoseconds).
+ */
+#define DDF_NOALLOC_MAX_ROWS (1 << 20)
+DDF_API ddf_status ddf_sptrsv_csr_noalloc(int32_t n, int64_t nnz, const int32_t* rowptr,
+                                          const int32_t* colidx, const double* values,
+                                          const double* b, double* x, int64_t spin_cap_ns,
+                                          ddf_stream_t s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,9 @@ RECORD_FIELDS = ("part", "type", "q0", "m", "n", "f_str", "rho", "g_str", "gamma
 EXPORTS = ("ddf_opts_default", "ddf_inspect", "ddf_update_values", "ddf_spmv", "ddf_sptrsv",
            "ddf_get_status", "ddf_plan_stats", "ddf_plan_export", "ddf_plan_destroy",
            "ddf_status_string", "ddf_last_launches", "ddf_kernel_launches",
-           "ddf_debug_set_dependency")
+           "ddf_debug_set_dependency", "ddf_sptrsv_csr_noalloc")
+#: rows accepted by ddf_sptrsv_csr_noalloc (the size of its static scratch)
+DDF_NOALLOC_MAX_ROWS = 1 << 20
 
 
 class DDFLibraryMissing(ImportError):
@@ -99,6 +101,8 @@ def lib():
         L.ddf_kernel_launches.argtypes = []
         L.ddf_kernel_launches.restype = I64
         L.ddf_debug_set_dependency.argtypes = [P, I64, I32]
+        L.ddf_sptrsv_csr_noalloc.argtypes = [I32, I64, P, P, P, P, P, I64, P]
+        L.ddf_sptrsv_csr_noalloc.restype = ctypes.c_int
         for name in ("ddf_inspect", "ddf_update_values", "ddf_spmv", "ddf_sptrsv", "ddf_get_status",
                      "ddf_plan_stats", "ddf_plan_export", "ddf_debug_set_dependency"):
             getattr(L, name).restype = ctypes.c_int
@@ -265,3 +269,23 @@ def ddf_kernel_launches() -> int:
 
 def ddf_debug_set_dependency(plan: Plan, k: int, col: int):
     _check(lib().ddf_debug_set_dependency(plan.handle, int(k), int(col)), "ddf_debug_set_dependency")
+
+
+def ddf_sptrsv_csr_noalloc(rowptr, colidx, values, b, x, spin_cap_ns: int = 2_000_000_000,
+                           stream=None) -> int:
+    """Solve L x = b on CUDA tensors without any device allocation (no plan).
+
+    Returns the status code (0 on success); synchronises the stream.
+    """
+    import torch
+    for t, name, dt in ((rowptr, "rowptr", torch.int32), (colidx, "colidx", torch.int32),
+                        (values, "values", torch.float64), (b, "b", torch.float64),
+                        (x, "x", torch.float64)):
+        if not (hasattr(t, "is_cuda") and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous CUDA {dt} tensor")
+    n = int(rowptr.numel()) - 1
+    return int(lib().ddf_sptrsv_csr_noalloc(n, int(colidx.numel()), ctypes.c_void_p(rowptr.data_ptr()),
+                                            ctypes.c_void_p(colidx.data_ptr()),
+                                            ctypes.c_void_p(values.data_ptr()),
+                                            ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                            int(spin_cap_ns), _stream(stream)))
