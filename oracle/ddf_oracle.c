@@ -368,8 +368,7 @@ int ora_inspect(int kind, int32_t n, const int32_t* Ap, const int32_t* Ai, int32
     int32_t* lev = NULL;
     if (!len || !cs) return ORA_ERR_OOM;
 
-    /* line 1: computeAccessFunctions; lines 2-3: findDependencies and
-     * partitionIterationSpace */
+    /* computeAccessFunctions, findDependencies and partitionIterationSpace */
     if (kind == ORA_SPMV) {
         for (int32_t i = 0; i < n; ++i) perm[i] = i;
         level_ptr[0] = 0;
@@ -430,17 +429,17 @@ int ora_inspect(int kind, int32_t n, const int32_t* Ap, const int32_t* Ai, int32
         goto done;
     }
 
-    for (int32_t p = 0; p < *nparts; ++p) {                 /* line 4 */
+    for (int32_t p = 0; p < *nparts; ++p) {                 /* each partition p */
         int32_t pb = level_ptr[p], pe = level_ptr[p + 1];
-        compute_fopd(&a, pb, pe, &d);                       /* line 5 */
-        for (int32_t ra = pb; ra < pe; ra += t) {           /* lines 6-7 */
+        compute_fopd(&a, pb, pe, &d);                       /* ComputeFOPD */
+        for (int32_t ra = pb; ra < pe; ra += t) {           /* GetConsecutiveIterations: regions */
             int32_t rb = (ra + t < pe) ? ra + t : pe;
             plist L[3] = {{bufs[0], 0}, {bufs[1], 0}, {bufs[2], 0}};
             int64_t C[3] = {-1, -1, -1};
-            if (allowed & ALLOW_BLAS) blas_first(&d, ra, rb, allowed, cov, &L[0]);   /* line 8 */
-            if (allowed & ALLOW_PSC1) psc1_first(&d, ra, rb, allowed, cov, &L[1]);   /* line 9 */
-            push(&L[2], T_PSC2, ra, rb);                                            /* line 10 */
-            int best = -1;                                                          /* line 11 */
+            if (allowed & ALLOW_BLAS) blas_first(&d, ra, rb, allowed, cov, &L[0]);   /* BLAS_first */
+            if (allowed & ALLOW_PSC1) psc1_first(&d, ra, rb, allowed, cov, &L[1]);   /* PSCI_first */
+            push(&L[2], T_PSC2, ra, rb);                                            /* PSCII_first */
+            int best = -1;                                                          /* min_cost */
             for (int s = 0; s < 3; ++s) {
                 if (s == 0 && !(allowed & ALLOW_BLAS)) continue;
                 if (s == 1 && !(allowed & ALLOW_PSC1)) continue;
@@ -449,7 +448,7 @@ int ora_inspect(int kind, int32_t n, const int32_t* Ap, const int32_t* Ai, int32
                 if (best < 0 || C[s] < C[best]) best = s;
             }
             qsort(L[best].v, (size_t)L[best].n, sizeof(piece), cmp_piece);
-            for (int32_t i = 0; i < L[best].n; ++i) {                               /* line 12 */
+            for (int32_t i = 0; i < L[best].n; ++i) {                               /* cList.append */
                 if (cnt == cap) {
                     cap *= 2;
                     int64_t* nr = (int64_t*)realloc(rec, sizeof(int64_t) * NF * (size_t)cap);
