@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-mixed", action="store_true")
     return ap.parse_args()
 
 
@@ -240,11 +241,85 @@ def run_ours(args, rank, world, local_rank):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, D, ddf, torch, dev, stream, exec_b, world)
+    mixed = None
+    if not args.no_mixed:
+        mixed = run_mixed(D, ddf, torch, stream, flush, breakdown)
 
     return {
         "value": value, "ms_per_step": ms, "wall_s": wall, "launches": launches, "clocks": clk,
         "breakdown": breakdown, "roofline": roofline, "e2e": e2e, "exec_bytes_per_step": exec_b,
+        "mixed": mixed,
     }
+
+
+def run_mixed(D, ddf, torch, stream, flush, breakdown, reps=5):
+    """FP32 / BF16 executors against the FP64 ones on the same matrices: SpMV
+    with low-precision values and vectors (FP32 sums), SpTRSV as low-precision
+    solves refined in FP64 to a relative residual of 1e-12.  Errors are stated
+    against the FP64 executor's result (itself within 1e-12 of the FP64 CPU
+    oracle in the parity tests)."""
+    out = {}
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    for d in D:
+        nm = d["name"]
+        a, lo = d["a"], d["lo"]
+        res = {}
+        p64 = ddf.ddf_inspect(*d["A"], a.n_cols, ddf.DDF_SPMV)
+        ddf.ddf_spmv(p64, d["x"], d["y"])
+        y64 = d["y"].clone()
+        t64 = timed(lambda: ddf.ddf_spmv(p64, d["x"], d["y"]))
+        st64 = ddf.ddf_plan_stats(p64)
+        res["spmv_f64_ms"] = round(t64, 4)
+        for dt, tdt, name, vs in ((ddf.DDF_F32, torch.float32, "f32", 4), (ddf.DDF_BF16, torch.bfloat16, "bf16", 2)):
+            pl = ddf.ddf_inspect(*d["A"], a.n_cols, ddf.DDF_SPMV, ddf.ddf_opts_default(store_dtype=dt))
+            xl = d["x"].to(tdt)
+            yl = torch.empty(a.n_rows, dtype=tdt, device=d["x"].device)
+            t = timed(lambda: ddf.ddf_spmv_lowp(pl, xl, yl))
+            err = float(torch.linalg.norm(yl.double() - y64) / torch.linalg.norm(y64))
+            lp_bytes = st64["bytes_exec"] - (8 - vs) * (st64["points"] + a.n_cols + a.n_rows)
+            res[f"spmv_{name}_ms"] = round(t, 4)
+            res[f"spmv_{name}_speedup"] = round(t64 / t, 3)
+            res[f"spmv_{name}_gbs"] = round(lp_bytes / (t * 1e-3) / 1e9, 1)
+            res[f"spmv_{name}_relerr"] = err
+            pl.destroy()
+        p64.destroy()
+        q64 = ddf.ddf_inspect(*d["L"], lo.n_cols, ddf.DDF_SPTRSV)
+        ddf.ddf_sptrsv(q64, d["b"], d["xs"])
+        x64 = d["xs"].clone()
+        tq = timed(lambda: ddf.ddf_sptrsv(q64, d["b"], d["xs"]))
+        res["sptrsv_f64_ms"] = round(tq, 4)
+        q64.destroy()
+        for dt, name in ((ddf.DDF_F32, "f32"), (ddf.DDF_BF16, "bf16")):
+            ql = ddf.ddf_inspect(*d["L"], lo.n_cols, ddf.DDF_SPTRSV, ddf.ddf_opts_default(store_dtype=dt))
+            xr = torch.empty(lo.n_rows, dtype=torch.float64, device=d["x"].device)
+            info = {}
+
+            def go():
+                info["r"] = ddf.ddf_sptrsv_refine(ql, d["b"], xr, tol=1e-12, max_iter=30)
+
+            t = timed(go)
+            st, iters, rel = info["r"]
+            res[f"sptrsv_refine_{name}_ms"] = round(t, 4)
+            res[f"sptrsv_refine_{name}_speedup"] = round(tq / t, 3)
+            res[f"sptrsv_refine_{name}_iters"] = iters
+            res[f"sptrsv_refine_{name}_relres"] = rel
+            res[f"sptrsv_refine_{name}_status"] = st
+            res[f"sptrsv_refine_{name}_relerr"] = float(torch.linalg.norm(xr - x64) / torch.linalg.norm(x64))
+            ql.destroy()
+        out[nm] = res
+    return out
 
 
 def run_e2e(args, D, ddf, torch, dev, stream, exec_b, world):
@@ -408,6 +483,7 @@ def main():
             "gpu_launches": r["launches"],
             "clocks": r["clocks"],
             "breakdown": r["breakdown"],
+            "mixed_precision": r["mixed"],
             "exec_bytes_per_step": r["exec_bytes_per_step"],
         }
         print(json.dumps(line))

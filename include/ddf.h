@@ -70,6 +70,9 @@ typedef enum {
 
 typedef enum { DDF_SPMV = 1, DDF_SPTRSV = 2 } ddf_kind;
 
+/* Storage types of plan values and of low-precision vectors. */
+typedef enum { DDF_F64 = 0, DDF_F32 = 1, DDF_BF16 = 2 } ddf_dtype;
+
 /* Codelet types (Sec. III-B): BLAS = f, g, h strided; PSC I = f, g strided and
  * h(i0,i1) = h0 + delta*i0 + s[i1] with one offset array s for all rows;
  * PSC II = the remaining runs, executed with per-nonzero column offsets. */
@@ -99,7 +102,9 @@ typedef struct {
     int64_t w_index;        /* Eq. 1 weight of one offset-array entry     (default 4 bytes)  */
     int64_t spin_cap_ns;    /* SpTRSV: longest wait on one dependency     (default 2e9 ns)   */
     int32_t unit_nnz;       /* executor work unit: target nonzeros per warp (default 256)     */
-    int32_t reserved[9];
+    int32_t store_dtype;    /* DDF_F64 (default), or DDF_F32 / DDF_BF16 for the mixed-precision
+                               executors (the plan then also keeps a low-precision copy)     */
+    int32_t reserved[8];
 } ddf_opts;
 
 /* Plan statistics (counts per codelet type are indexed by ddf_codelet_type). */
@@ -157,6 +162,30 @@ DDF_API ddf_status ddf_spmv(ddf_plan_t p, const double* x, double* y, ddf_stream
  * plan's status word (read it with ddf_get_status) and the solve finishes
  * with NaN in the affected rows instead of hanging. */
 DDF_API ddf_status ddf_sptrsv(ddf_plan_t p, const double* b, double* x, ddf_stream_t s);
+
+/*
+ * Mixed-precision SpMV (a later form of the executor, beyond the paper's FP64
+ * codelets): the plan must have been inspected with store_dtype DDF_F32 or
+ * DDF_BF16.  y = A x with the values in that type, x and y device vectors of
+ * vec_dtype (DDF_F32 or DDF_BF16), every product and sum in FP32.  Same
+ * codelets and kernels per type as ddf_spmv.
+ */
+DDF_API ddf_status ddf_spmv_lowp(ddf_plan_t p, const void* x, void* y, ddf_dtype vec_dtype, ddf_stream_t s);
+
+/*
+ * Mixed-precision SpTRSV with iterative refinement.  The plan (kind
+ * DDF_SPTRSV, store_dtype DDF_F32 or DDF_BF16) keeps the FP64 values as well.
+ * x0 = solve(b) in low precision (FP32 vectors, FP32 sums); then repeatedly
+ * r = b - L x in FP64, stop once ||r||_2 <= tol ||b||_2, else d = solve(r) in
+ * low precision and x += d in FP64.  The residual and the update are the only
+ * FP64 steps.  b and x are FP64 device vectors.  *iters receives the number
+ * of corrections applied, *relres the last relative residual (either may be
+ * NULL).  Synchronises s once per refinement step.  Returns
+ * DDF_ERR_NOT_CONVERGED when max_iter corrections do not reach tol (x then
+ * holds the last iterate) and DDF_ERR_TIMEOUT when a solve's wait ran out.
+ */
+DDF_API ddf_status ddf_sptrsv_refine(ddf_plan_t p, const double* b, double* x, double tol, int32_t max_iter,
+                                     ddf_stream_t s, int32_t* iters, double* relres);
 
 /* Synchronise s, then return and clear the plan's device status word. */
 DDF_API ddf_status ddf_get_status(ddf_plan_t p, ddf_stream_t s);

@@ -21,6 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libddf.so")
 
 DDF_SPMV, DDF_SPTRSV = 1, 2
+DDF_F64, DDF_F32, DDF_BF16 = 0, 1, 2
 DDF_BLAS, DDF_PSC1, DDF_PSC2 = 0, 1, 2
 DDF_ALLOW_BLAS, DDF_ALLOW_PSC1, DDF_ALLOW_PSC2, DDF_ALLOW_ALL = 1, 2, 4, 7
 STATUS = {0: "DDF_OK", 1: "DDF_ERR_ARG", 2: "DDF_ERR_NOT_SQUARE", 3: "DDF_ERR_UNSORTED",
@@ -33,7 +34,7 @@ RECORD_FIELDS = ("part", "type", "q0", "m", "n", "f_str", "rho", "g_str", "gamma
 EXPORTS = ("ddf_opts_default", "ddf_inspect", "ddf_update_values", "ddf_spmv", "ddf_sptrsv",
            "ddf_get_status", "ddf_plan_stats", "ddf_plan_export", "ddf_plan_destroy",
            "ddf_status_string", "ddf_last_launches", "ddf_kernel_launches",
-           "ddf_debug_set_dependency", "ddf_sptrsv_csr_noalloc")
+           "ddf_debug_set_dependency", "ddf_sptrsv_csr_noalloc", "ddf_spmv_lowp", "ddf_sptrsv_refine")
 #: rows accepted by ddf_sptrsv_csr_noalloc (the size of its static scratch)
 DDF_NOALLOC_MAX_ROWS = 1 << 20
 
@@ -58,7 +59,7 @@ class ddf_opts(ctypes.Structure):
     _fields_ = [("window_t", ctypes.c_int32), ("allowed_types", ctypes.c_int32),
                 ("w_op", ctypes.c_int64), ("w_codelet", ctypes.c_int64), ("w_index", ctypes.c_int64),
                 ("spin_cap_ns", ctypes.c_int64), ("unit_nnz", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 9)]
+                ("store_dtype", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
 
 
 class ddf_plan_stats_t(ctypes.Structure):
@@ -101,6 +102,11 @@ def lib():
         L.ddf_kernel_launches.argtypes = []
         L.ddf_kernel_launches.restype = I64
         L.ddf_debug_set_dependency.argtypes = [P, I64, I32]
+        L.ddf_spmv_lowp.argtypes = [P, P, P, ctypes.c_int, P]
+        L.ddf_spmv_lowp.restype = ctypes.c_int
+        L.ddf_sptrsv_refine.argtypes = [P, P, P, ctypes.c_double, I32, P, ctypes.POINTER(I32),
+                                        ctypes.POINTER(ctypes.c_double)]
+        L.ddf_sptrsv_refine.restype = ctypes.c_int
         L.ddf_sptrsv_csr_noalloc.argtypes = [I32, I64, P, P, P, P, P, I64, P]
         L.ddf_sptrsv_csr_noalloc.restype = ctypes.c_int
         for name in ("ddf_inspect", "ddf_update_values", "ddf_spmv", "ddf_sptrsv", "ddf_get_status",
@@ -221,6 +227,32 @@ def ddf_sptrsv(plan: Plan, b, x, stream=None):
     """Solve L x = b on the device (asynchronous on the stream)."""
     _check(lib().ddf_sptrsv(plan.handle, _dev_vec(b, plan.n_rows, "b"), _dev_vec(x, plan.n_rows, "x"),
                             _stream(stream)), "ddf_sptrsv")
+
+
+def _lp_vec(t, n, name):
+    import torch
+    if not (hasattr(t, "is_cuda") and t.is_cuda) or t.dtype not in (torch.float32, torch.bfloat16) \
+            or not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name} must be a contiguous float32 or bfloat16 CUDA tensor with {n} entries")
+    return ctypes.c_void_p(t.data_ptr()), (DDF_F32 if t.dtype == torch.float32 else DDF_BF16)
+
+
+def ddf_spmv_lowp(plan: Plan, x, y, stream=None):
+    """y = A x with FP32 / BF16 values and vectors, FP32 sums (plan store_dtype F32 or BF16)."""
+    px, dx = _lp_vec(x, plan.n_cols, "x")
+    py, dy = _lp_vec(y, plan.n_rows, "y")
+    if dx != dy:
+        raise ValueError("x and y must have the same dtype")
+    _check(lib().ddf_spmv_lowp(plan.handle, px, py, dx, _stream(stream)), "ddf_spmv_lowp")
+
+
+def ddf_sptrsv_refine(plan: Plan, b, x, tol: float = 1e-12, max_iter: int = 20, stream=None):
+    """Solve L x = b by low-precision solves and FP64 refinement; returns (status, iters, relres)."""
+    it = ctypes.c_int32(0)
+    rr = ctypes.c_double(0.0)
+    st = lib().ddf_sptrsv_refine(plan.handle, _dev_vec(b, plan.n_rows, "b"), _dev_vec(x, plan.n_rows, "x"),
+                                 float(tol), int(max_iter), _stream(stream), ctypes.byref(it), ctypes.byref(rr))
+    return int(st), int(it.value), float(rr.value)
 
 
 def ddf_get_status(plan: Plan, stream=None) -> int:

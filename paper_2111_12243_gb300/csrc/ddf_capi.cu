@@ -40,6 +40,14 @@ void release(ddf_plan_s* p) {
     for (int k = 0; k < 3; ++k) ddf_free(p->units[k], s);
     ddf_free(p->status, s);
     ddf_free(p->ticket, s);
+    if (p->val_lp) (void)cudaFreeAsync(p->val_lp, s);
+    p->val_lp = nullptr;
+    ddf_free(p->dinv_lp, s);
+    ddf_free(p->diag, s);
+    ddf_free(p->r64, s);
+    ddf_free(p->rlp, s);
+    ddf_free(p->xlp, s);
+    ddf_free(p->nrm, s);
 }
 
 ddf_status check_opts(const ddf_opts* o) {
@@ -47,6 +55,7 @@ ddf_status check_opts(const ddf_opts* o) {
     if (!(o->allowed_types & DDF_ALLOW_PSC2) || (o->allowed_types & ~DDF_ALLOW_ALL)) return DDF_ERR_ARG;
     if (o->w_op < 0 || o->w_codelet < 0 || o->w_index < 0) return DDF_ERR_ARG;
     if (o->spin_cap_ns <= 0 || o->unit_nnz < 1) return DDF_ERR_ARG;
+    if (o->store_dtype != DDF_F64 && o->store_dtype != DDF_F32 && o->store_dtype != DDF_BF16) return DDF_ERR_ARG;
     return DDF_OK;
 }
 
@@ -183,6 +192,8 @@ ddf_status ddf_inspect(const ddf_csr* A, ddf_kind kind, const ddf_opts* o, ddf_s
         ddf_free(ci, s);
         ddf_free(v, s);
     }
+    if (!st) st = ddf_make_lowp(p, s);
+    if (!st && cudaStreamSynchronize(s) != cudaSuccess) st = DDF_ERR_CUDA;
     if (st) {
         release(p);
         (void)cudaStreamSynchronize(s);
@@ -220,6 +231,7 @@ ddf_status ddf_update_values(ddf_plan_t p, const double* values, int32_t on_devi
         }
     }
     if (!st) st = ddf_gather_values(p, src, s);
+    if (!st) st = ddf_make_lowp(p, s);
     ddf_free(v, s);
     return st;
 }
@@ -246,6 +258,37 @@ ddf_status ddf_sptrsv(ddf_plan_t p, const double* b, double* x, ddf_stream_t str
         return DDF_OK;
     }
     return ddf_launch_sptrsv(p, b, x, (cudaStream_t)stream);
+}
+
+ddf_status ddf_spmv_lowp(ddf_plan_t p, const void* x, void* y, ddf_dtype vec_dtype, ddf_stream_t stream) {
+    if (!p) return DDF_ERR_ARG;
+    if (p->kind != DDF_SPMV) return DDF_ERR_WRONG_KIND;
+    if (p->vdtype != DDF_F32 && p->vdtype != DDF_BF16) return DDF_ERR_ARG;
+    if (vec_dtype != DDF_F32 && vec_dtype != DDF_BF16) return DDF_ERR_ARG;
+    if ((p->n > 0 && !y) || (p->n_cols > 0 && !x) || (p->nnz > 0 && !p->has_values)) return DDF_ERR_ARG;
+    if (p->n == 0) {
+        p->last_launches = 0;
+        return DDF_OK;
+    }
+    return ddf_launch_spmv_lp(p, x, y, vec_dtype, (cudaStream_t)stream);
+}
+
+ddf_status ddf_sptrsv_refine(ddf_plan_t p, const double* b, double* x, double tol, int32_t max_iter,
+                             ddf_stream_t stream, int32_t* iters, double* relres) {
+    if (!p) return DDF_ERR_ARG;
+    if (p->kind != DDF_SPTRSV) return DDF_ERR_WRONG_KIND;
+    if (p->vdtype != DDF_F32 && p->vdtype != DDF_BF16) return DDF_ERR_ARG;
+    if (!(tol >= 0.0) || max_iter < 0) return DDF_ERR_ARG;
+    if (p->n > 0 && (!b || !x || !p->has_values)) return DDF_ERR_ARG;
+    if (p->n > 0 && (const void*)b < (const void*)(x + p->n) && (const void*)x < (const void*)(b + p->n))
+        return DDF_ERR_ARG;
+    if (p->n == 0) {
+        if (iters) *iters = 0;
+        if (relres) *relres = 0.0;
+        p->last_launches = 0;
+        return DDF_OK;
+    }
+    return ddf_refine(p, b, x, tol, max_iter, (cudaStream_t)stream, iters, relres);
 }
 
 ddf_status ddf_get_status(ddf_plan_t p, ddf_stream_t stream) {

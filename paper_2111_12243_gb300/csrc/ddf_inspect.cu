@@ -109,14 +109,17 @@ __device__ int32_t wait_level(const int32_t* p, int32_t* status, int64_t cap_ns)
     }
 }
 
-// Bounded wait on a level written by another warp of this CTA.
+// Bounded wait on a level written by another warp of this CTA.  The wait
+// sleeps between polls: a warp spinning on shared memory would otherwise take
+// issue slots from the warp of its SM that computes the awaited row.
 __device__ int32_t wait_level_smem(volatile int32_t* p, int32_t* status, int64_t cap_ns) {
     uint64_t t0 = ddf_globaltimer();
     uint32_t it = 0;
     while (true) {
         int32_t v = *p;
         if (v >= 0) return v;
-        if ((++it & 255u) == 0) {
+        if (++it > 4) __nanosleep(64);
+        if ((it & 63u) == 0) {
             if (ddf_ld_relaxed_s32(status) != 0) return 0;
             if ((int64_t)(ddf_globaltimer() - t0) > cap_ns) {
                 ddf_set_status(status, DDF_ERR_TIMEOUT);
@@ -130,9 +133,27 @@ __device__ int32_t wait_level_smem(volatile int32_t* p, int32_t* status, int64_t
 // warp w computes rows [w*LEV_RPW, (w+1)*LEV_RPW) of the chunk in order.
 // Levels of the chunk's rows are also kept in shared memory: a dependency
 // inside the chunk (the common case for banded and stencil matrices) costs a
-// shared-memory read instead of an L2 round trip.  Every row waited on has a
-// smaller index, so it belongs to this CTA or to a CTA that already holds a
-// ticket and runs: the waits end.
+// shared-memory read instead of an L2 round trip.  The rows are software
+// pipelined: while row rr is reduced, the column indices of row rr + 1 and
+// the levels of its dependencies outside the chunk are already in flight, so
+// the chain from one row to the next only holds shared-memory work.  Every
+// row waited on has a smaller index, so it belongs to this CTA or to a CTA
+// that already holds a ticket and runs: the waits end.
+constexpr int LEV_PF = 2;   // dependencies per lane prefetched (rows of up to 64 off-diagonals)
+
+__device__ __forceinline__ void lev_prefetch(int32_t a, int32_t b, int lane, int64_t base,
+                                             const int32_t* __restrict__ ci, const int32_t* lev,
+                                             int32_t* j, int32_t* l) {
+#pragma unroll
+    for (int k = 0; k < LEV_PF; ++k) {
+        const int32_t kk = a + lane + 32 * k;
+        j[k] = kk < b ? ci[kk] : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < LEV_PF; ++k)
+        l[k] = (j[k] >= 0 && (int64_t)j[k] < base) ? ddf_ld_relaxed_s32(lev + j[k]) : -1;
+}
+
 __global__ void __launch_bounds__(DDF_CTA_THREADS)
 k_levels(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int32_t* lev,
          uint32_t* ticket, int32_t* maxlev, int32_t* status, int64_t cap_ns) {
@@ -153,20 +174,47 @@ k_levels(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ 
         ra_l = rp[r0 + lane];
         rb_l = rp[r0 + lane + 1] - 1;   // the diagonal is last: not a dependency
     }
+    int32_t cj[LEV_PF], cl[LEV_PF];
+    {
+        const int32_t a = __shfl_sync(0xffffffffu, ra_l, 0), b = __shfl_sync(0xffffffffu, rb_l, 0);
+        lev_prefetch(a, r0 < n ? b : a, lane, base, ci, lev, cj, cl);
+    }
     for (int rr = 0; rr < LEV_RPW; ++rr) {
         const int64_t r = r0 + rr;
         if (r >= n) break;
         const int32_t a = __shfl_sync(0xffffffffu, ra_l, rr), b = __shfl_sync(0xffffffffu, rb_l, rr);
+        // next row's columns and external levels go out now
+        int32_t nj[LEV_PF], nl[LEV_PF];
+        {
+            const bool more = rr + 1 < LEV_RPW && r + 1 < n;
+            const int32_t na = __shfl_sync(0xffffffffu, ra_l, (rr + 1) & 31);
+            const int32_t nb = __shfl_sync(0xffffffffu, rb_l, (rr + 1) & 31);
+            lev_prefetch(na, more ? nb : na, lane, base, ci, lev, nj, nl);
+        }
         int32_t m = -1;
-        for (int32_t k = a + lane; k < b; k += 32) {
-            const int32_t j = ci[k];
+#pragma unroll
+        for (int k = 0; k < LEV_PF; ++k) {
+            const int32_t jj = cj[k];
+            if (jj < 0) continue;
             int32_t lj;
-            if ((int64_t)j >= base) {
-                lj = vs[j - base];
-                if (lj < 0) lj = wait_level_smem(vs + (j - base), status, cap_ns);
+            if ((int64_t)jj >= base) {
+                lj = vs[jj - base];
+                if (lj < 0) lj = wait_level_smem(vs + (jj - base), status, cap_ns);
             } else {
-                lj = ddf_ld_relaxed_s32(lev + j);
-                if (lj < 0) lj = wait_level(lev + j, status, cap_ns);
+                lj = cl[k];
+                if (lj < 0) lj = wait_level(lev + jj, status, cap_ns);
+            }
+            m = max(m, lj);
+        }
+        for (int32_t k = a + lane + 32 * LEV_PF; k < b; k += 32) {   // rows longer than the prefetch
+            const int32_t jj = ci[k];
+            int32_t lj;
+            if ((int64_t)jj >= base) {
+                lj = vs[jj - base];
+                if (lj < 0) lj = wait_level_smem(vs + (jj - base), status, cap_ns);
+            } else {
+                lj = ddf_ld_relaxed_s32(lev + jj);
+                if (lj < 0) lj = wait_level(lev + jj, status, cap_ns);
             }
             m = max(m, lj);
         }
@@ -178,6 +226,11 @@ k_levels(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ 
         }
         mymax = max(mymax, m + 1);
         __syncwarp();
+#pragma unroll
+        for (int k = 0; k < LEV_PF; ++k) {
+            cj[k] = nj[k];
+            cl[k] = nl[k];
+        }
     }
     if (lane == 0) wmax[w] = mymax;
     __syncthreads();
@@ -212,7 +265,7 @@ __global__ void k_rel_lens(int32_t n, const int32_t* __restrict__ perm, const in
 __global__ void k_rel_gather(int32_t n, const int32_t* __restrict__ perm, const int32_t* __restrict__ rp,
                              const int32_t* __restrict__ ci, const double* __restrict__ vals,
                              const int32_t* __restrict__ st, int32_t* __restrict__ col,
-                             double* __restrict__ val, double* __restrict__ dinv) {
+                             double* __restrict__ val, double* __restrict__ dinv, double* __restrict__ diag) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     int32_t r = perm[q];
@@ -221,6 +274,7 @@ __global__ void k_rel_gather(int32_t n, const int32_t* __restrict__ perm, const 
     if (vals) {
         for (int32_t k = a; k < e; ++k) val[d + (k - a)] = vals[k];
         dinv[q] = 1.0 / vals[e];
+        if (diag) diag[q] = vals[e];
     }
 }
 
@@ -670,13 +724,76 @@ __device__ int32_t make_units(const dcod& c, int32_t ci, const int32_t* __restri
     return cnt;
 }
 
+// SpMV BLAS / PSC I codelets smaller than one unit are grouped: consecutive
+// codelets of one type and one row length whose rows are contiguous share a
+// work unit (encoded with i0b = -count, i0e = total rows), so that a warp
+// amortises its descriptor loads over several small codelets.
+constexpr int32_t GROUP_MAX_ROWS = 256;
+constexpr int32_t GROUP_MAX_CODELETS = 32;
+
+__device__ __forceinline__ int32_t spmv_lanes(int32_t n) {
+    int32_t v = 1;
+    while (v < 32 && (int64_t)(32 / v) * n * 8 > SPMV_WARP_SPAN) v <<= 1;
+    return v;
+}
+__device__ __forceinline__ int32_t spmv_unit_rows(int32_t n, int32_t unit_nnz) {
+    int32_t rpw = 32 / spmv_lanes(n);
+    return rpw * max(1, (n > 0) ? unit_nnz / (rpw * n) : 32);
+}
+__device__ __forceinline__ bool groupable(const dcod& c, int32_t unit_nnz) {
+    return c.type != DDF_PSC2 && c.m < spmv_unit_rows(c.n, unit_nnz);
+}
+__device__ __forceinline__ bool linked(const dcod& p, const dcod& c, int32_t unit_nnz) {
+    return groupable(p, unit_nnz) && groupable(c, unit_nnz) && p.type == c.type && p.n == c.n &&
+           p.q0 + p.m == c.q0;
+}
+
+// Group units led by codelet i (which starts a chain of linked codelets).
+template <bool WRITE>
+__device__ int32_t make_groups(const dcod* __restrict__ cod, int64_t ncod, int64_t i, int32_t unit_nnz,
+                               dunit* out) {
+    const dcod c0 = cod[i];
+    const int32_t cap = min(GROUP_MAX_ROWS, 4 * spmv_unit_rows(c0.n, unit_nnz));
+    const int32_t v = spmv_lanes(c0.n);
+    int32_t cnt = 0;
+    int64_t g = i;
+    int32_t rows = c0.m, k = 1;
+    dcod prev = c0;
+    for (int64_t j = i + 1;; ++j) {
+        bool more = j < ncod;
+        dcod cj;
+        if (more) {
+            cj = cod[j];
+            more = linked(prev, cj, unit_nnz);
+        }
+        if (!more || rows + cj.m > cap || k == GROUP_MAX_CODELETS) {
+            if (WRITE) out[cnt] = (k == 1) ? dunit{(int32_t)g, 0, rows, v} : dunit{(int32_t)g, -k, rows, v};
+            ++cnt;
+            if (!more) break;
+            g = j;
+            rows = 0;
+            k = 0;
+        }
+        rows += cj.m;
+        ++k;
+        prev = cj;
+    }
+    return cnt;
+}
+
 __global__ void k_unit_counts(int64_t ncod, const dcod* __restrict__ cod, const int32_t* __restrict__ st,
                               int32_t unit_nnz, int split_types, int32_t* __restrict__ c0,
                               int32_t* __restrict__ c1, int32_t* __restrict__ c2) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ncod) return;
     dcod c = cod[i];
-    int32_t k = make_units<false>(c, (int32_t)i, st, unit_nnz, !split_types, nullptr);
+    int32_t k;
+    if (split_types && groupable(c, unit_nnz)) {
+        // members of a chain add nothing; the chain's first codelet makes its groups
+        k = (i > 0 && linked(cod[i - 1], c, unit_nnz)) ? 0 : make_groups<false>(cod, ncod, i, unit_nnz, nullptr);
+    } else {
+        k = make_units<false>(c, (int32_t)i, st, unit_nnz, !split_types, nullptr);
+    }
     if (!split_types) {
         c0[i] = k;
         return;
@@ -698,6 +815,10 @@ __global__ void k_unit_write(int64_t ncod, const dcod* __restrict__ cod, const i
     else if (c.type == DDF_BLAS) dst = u0 + o0[i];
     else if (c.type == DDF_PSC1) dst = u1 + o1[i];
     else dst = u2 + o2[i];
+    if (split_types && groupable(c, unit_nnz)) {
+        if (!(i > 0 && linked(cod[i - 1], c, unit_nnz))) make_groups<true>(cod, ncod, i, unit_nnz, dst);
+        return;
+    }
     make_units<true>(c, (int32_t)i, st, unit_nnz, !split_types, dst);
 }
 
@@ -844,9 +965,10 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
         TRY(ddf_alloc(&p->col, npts, s));
         TRY(ddf_alloc(&p->val, npts, s));
         TRY(ddf_alloc(&p->dinv, n, s));
+        if (p->opts.store_dtype != DDF_F64) TRY(ddf_alloc(&p->diag, n, s));
         if (n > 0) {
             k_rel_gather<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, p->seq, rowptr, colidx, values, p->starts,
-                                                        p->col, p->val, p->dinv);
+                                                        p->col, p->val, p->dinv, p->diag);
             ddf_count_launch();
         }
         DDF_CUDA_TRY(cudaGetLastError());
@@ -1015,7 +1137,7 @@ ddf_status ddf_gather_values(ddf_plan_s* p, const double* values, cudaStream_t s
     int32_t n = p->n;
     if (n > 0) {
         k_rel_gather<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, p->seq, p->orig_rowptr, nullptr, values,
-                                                    p->starts, nullptr, p->val, p->dinv);
+                                                    p->starts, nullptr, p->val, p->dinv, p->diag);
         ddf_count_launch();
     }
     DDF_CUDA_TRY(cudaGetLastError());

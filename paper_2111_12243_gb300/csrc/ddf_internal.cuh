@@ -2,6 +2,7 @@
 // Nothing here is part of the public ABI (include/ddf.h is).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -67,6 +68,16 @@ struct ddf_plan_s {
     int32_t last_launches;
     int32_t units_per_cta;
     int32_t sm_count;
+    // mixed precision (store_dtype != DDF_F64): low-precision copies and the
+    // refinement scratch of a SpTRSV plan
+    int32_t vdtype;
+    void* val_lp;                 // values in store_dtype, same layout as val
+    float* dinv_lp;               // SpTRSV: 1 / L_ii rounded to FP32
+    double* diag;                 // SpTRSV: L_ii in FP64 (residual)
+    double* r64;                  // residual b - L x (row order)
+    float* rlp;                   // residual rounded to FP32 (right-hand side of a correction)
+    float* xlp;                   // low-precision solution / correction
+    double* nrm;                  // two FP64 accumulators (||b||^2, ||r||^2)
     // statistics, computed on the first ddf_plan_stats call
     int32_t stats_ready;
     ddf_plan_stats_t stats;
@@ -84,6 +95,18 @@ struct ddf_plan_s {
         }                                          \
     } while (0)
 
+// value conversions used by the templated executors
+template <typename TA>
+__device__ __forceinline__ TA ddf_cvt(double v) { return (TA)v; }
+template <typename TA>
+__device__ __forceinline__ TA ddf_cvt(float v) { return (TA)v; }
+template <typename TA>
+__device__ __forceinline__ TA ddf_cvt(__nv_bfloat16 v) { return (TA)__bfloat162float(v); }
+template <typename T>
+__device__ __forceinline__ T ddf_from_float(float v) { return (T)v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 ddf_from_float<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
 // ---------------------------------------------------------------------------
 // memory-model helpers (inline PTX)
 // ---------------------------------------------------------------------------
@@ -94,6 +117,14 @@ __device__ __forceinline__ unsigned long long ddf_ld_relaxed_u64(const void* p) 
 }
 __device__ __forceinline__ void ddf_st_relaxed_u64(void* p, unsigned long long v) {
     asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ddf_ld_relaxed_u32(const void* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void ddf_st_relaxed_u32(void* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ int32_t ddf_ld_relaxed_s32(const void* p) {
     int32_t v;
@@ -127,8 +158,14 @@ ddf_status ddf_gather_values(ddf_plan_s* p, const double* values, cudaStream_t s
 ddf_status ddf_compute_stats(ddf_plan_s* p);
 // ddf_spmv.cu
 ddf_status ddf_launch_spmv(ddf_plan_s* p, const double* x, double* y, cudaStream_t s);
+ddf_status ddf_launch_spmv_lp(ddf_plan_s* p, const void* x, void* y, int vec_dtype, cudaStream_t s);
 // ddf_sptrsv.cu
 ddf_status ddf_launch_sptrsv(ddf_plan_s* p, const double* b, double* x, cudaStream_t s);
+ddf_status ddf_launch_sptrsv_lp(ddf_plan_s* p, const float* b, float* x, cudaStream_t s);
+// ddf_mixed.cu
+ddf_status ddf_make_lowp(ddf_plan_s* p, cudaStream_t s);
+ddf_status ddf_refine(ddf_plan_s* p, const double* b, double* x, double tol, int32_t max_iter, cudaStream_t s,
+                      int32_t* iters, double* relres);
 
 // process-wide count of kernel launches (ddf_capi.cu)
 void ddf_count_launch(int64_t k = 1);

@@ -10,27 +10,111 @@
 //   PSC II col[g(i0, i1)]                    one index per point, row extents from starts
 // Values of BLAS / PSC I codelets sit at g0 + gamma*i0 + i1: consecutive rows
 // are contiguous, so a row group's loads are coalesced.
+//
+// The kernels are templated on the value type TV, the vector types TX / TY
+// and the accumulator TA: FP64 throughout for ddf_spmv, and FP32 / BF16
+// storage with FP32 products and sums for ddf_spmv_lowp.
 #include "ddf_internal.cuh"
 
 namespace {
 
 constexpr int SMAX = 4;   // s entries kept in registers per lane (n <= 4 v)
 
-template <int TYPE>
+// One row of a BLAS / PSC I codelet: lanes li, li + v, ... of its row group.
+template <int TYPE, typename TV, typename TX, typename TA>
+__device__ __forceinline__ TA row_strided(const TV* __restrict__ val, const TX* __restrict__ x,
+                                          const int32_t* __restrict__ col, int32_t n, int32_t v, int32_t li,
+                                          int32_t g, int32_t hb, int32_t sigma, int32_t sref, int32_t h0,
+                                          const int32_t* sreg) {
+    TA acc = 0;
+    const TV* vp = val + g;
+    if (TYPE == DDF_BLAS) {
+#pragma unroll 4
+        for (int32_t i1 = li; i1 < n; i1 += v)
+            acc += ddf_cvt<TA>(__ldcs(vp + i1)) * ddf_cvt<TA>(__ldg(x + hb + sigma * i1));
+    } else if (sreg != nullptr && n <= SMAX * v) {
+#pragma unroll
+        for (int k = 0; k < SMAX; ++k) {
+            int32_t i1 = li + k * v;
+            if (i1 < n) acc += ddf_cvt<TA>(__ldcs(vp + i1)) * ddf_cvt<TA>(__ldg(x + hb + sreg[k]));
+        }
+    } else {
+        const int32_t* sp = col + sref;
+#pragma unroll 4
+        for (int32_t i1 = li; i1 < n; i1 += v)
+            acc += ddf_cvt<TA>(__ldcs(vp + i1)) * ddf_cvt<TA>(__ldg(x + hb + (__ldg(sp + i1) - h0)));
+    }
+    return acc;
+}
+
+template <typename TY, typename TA>
+__device__ __forceinline__ TY store_cvt(TA v) { return (TY)v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 store_cvt<__nv_bfloat16, float>(float v) { return __float2bfloat16_rn(v); }
+
+template <int TYPE, typename TV, typename TX, typename TY, typename TA>
 __global__ void __launch_bounds__(DDF_CTA_THREADS)
 k_spmv(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64_t nunits,
-       const int32_t* __restrict__ st, const int32_t* __restrict__ col, const double* __restrict__ val,
-       const double* __restrict__ x, double* __restrict__ y) {
-    const int lane = threadIdx.x & 31;
+       const int32_t* __restrict__ st, const int32_t* __restrict__ col, const TV* __restrict__ val,
+       const TX* __restrict__ x, TY* __restrict__ y) {
+    __shared__ int8_t rowslot[DDF_WARPS_PER_CTA][256];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nunits; u += nw) {
         const dunit U = units[u];
-        const dcod C = cod[U.cod];
         const int v = U.v;
         const int lg = __ffs(v) - 1;
         const int rpw = 32 >> lg;
         const int sub = lane >> lg;
         const int li = lane & (v - 1);
+        if (TYPE != DDF_PSC2 && U.i0b < 0) {
+            // group of -U.i0b small codelets with U.i0e rows in total: lane k holds
+            // codelet k's descriptor, rowslot maps a unit row to its codelet
+            const int cnt = -U.i0b;
+            dcod C;
+            int32_t m = 0;
+            if (lane < cnt) {
+                C = cod[U.cod + lane];
+                m = C.m;
+            } else {
+                C = cod[U.cod];
+            }
+            int32_t incl = m;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int32_t excl = incl - m;
+            __syncwarp();
+            for (int32_t r = excl; r < incl; ++r) rowslot[wl][r] = (int8_t)lane;
+            __syncwarp();
+            const int32_t n = C.n;   // equal for every codelet of the group (lane 0's is used)
+            const int32_t n0 = __shfl_sync(0xffffffffu, n, 0);
+            for (int32_t kb = 0; kb < U.i0e; kb += rpw) {
+                const int32_t k = kb + sub;
+                const bool act = k < U.i0e;
+                const int slot = act ? rowslot[wl][k] : 0;
+                const int32_t i0 = k - __shfl_sync(0xffffffffu, excl, slot);
+                const int32_t f0 = __shfl_sync(0xffffffffu, C.f0, slot);
+                const int32_t rho = __shfl_sync(0xffffffffu, C.rho, slot);
+                const int32_t g0 = __shfl_sync(0xffffffffu, C.g0, slot);
+                const int32_t gamma = __shfl_sync(0xffffffffu, C.gamma, slot);
+                const int32_t h0 = __shfl_sync(0xffffffffu, C.h0, slot);
+                const int32_t delta = __shfl_sync(0xffffffffu, C.delta, slot);
+                const int32_t sigma = __shfl_sync(0xffffffffu, C.sigma, slot);
+                const int32_t sref = __shfl_sync(0xffffffffu, C.sref, slot);
+                TA acc = 0;
+                if (act)
+                    acc = row_strided<TYPE, TV, TX, TA>(val, x, col, n0, v, li, g0 + gamma * i0, h0 + delta * i0,
+                                                        sigma, sref, h0, nullptr);
+                for (int o = v >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (act && li == 0) y[f0 + rho * i0] = store_cvt<TY, TA>(acc);
+            }
+            __syncwarp();
+            continue;
+        }
+        const dcod C = cod[U.cod];
         int32_t sreg[SMAX];
         if (TYPE == DDF_PSC1) {
 #pragma unroll
@@ -42,39 +126,23 @@ k_spmv(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64_t nu
         for (int32_t ib = U.i0b; ib < U.i0e; ib += rpw) {
             const int32_t i0 = ib + sub;
             const bool act = i0 < U.i0e;
-            double acc = 0.0;
+            TA acc = 0;
             int32_t r = 0;
             if (act) {
                 r = C.f0 + C.rho * i0;
-                if (TYPE == DDF_BLAS) {
-                    const double* vp = val + (C.g0 + C.gamma * i0);
-                    const int32_t hb = C.h0 + C.delta * i0;
-#pragma unroll 8
-                    for (int32_t i1 = li; i1 < C.n; i1 += v) acc += __ldcs(vp + i1) * __ldg(x + hb + C.sigma * i1);
-                } else if (TYPE == DDF_PSC1) {
-                    const double* vp = val + (C.g0 + C.gamma * i0);
-                    const int32_t hb = C.h0 + C.delta * i0;
-                    if (C.n <= SMAX * v) {
-#pragma unroll
-                        for (int k = 0; k < SMAX; ++k) {
-                            int32_t i1 = li + k * v;
-                            if (i1 < C.n) acc += __ldcs(vp + i1) * __ldg(x + hb + sreg[k]);
-                        }
-                    } else {
-                        const int32_t* sp = col + C.sref;
-#pragma unroll 8
-                        for (int32_t i1 = li; i1 < C.n; i1 += v)
-                            acc += __ldcs(vp + i1) * __ldg(x + hb + (__ldg(sp + i1) - C.h0));
-                    }
-                } else {
+                if (TYPE == DDF_PSC2) {
                     const int32_t q = C.q0 + i0;
                     const int32_t kb = st[q], ke = st[q + 1];
 #pragma unroll 4
-                    for (int32_t k = kb + li; k < ke; k += v) acc += __ldcs(val + k) * __ldg(x + __ldcs(col + k));
+                    for (int32_t k = kb + li; k < ke; k += v)
+                        acc += ddf_cvt<TA>(__ldcs(val + k)) * ddf_cvt<TA>(__ldg(x + __ldcs(col + k)));
+                } else {
+                    acc = row_strided<TYPE, TV, TX, TA>(val, x, col, C.n, v, li, C.g0 + C.gamma * i0,
+                                                        C.h0 + C.delta * i0, C.sigma, C.sref, C.h0, sreg);
                 }
             }
             for (int o = v >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (act && li == 0) y[r] = acc;
+            if (act && li == 0) y[r] = store_cvt<TY, TA>(acc);
         }
     }
 }
@@ -87,30 +155,53 @@ unsigned grid_for(int64_t nunits, int sm_count) {
     return (unsigned)ctas;
 }
 
-}  // namespace
-
-ddf_status ddf_launch_spmv(ddf_plan_s* p, const double* x, double* y, cudaStream_t s) {
+template <typename TV, typename TX, typename TY, typename TA>
+int launch_all(ddf_plan_s* p, const TV* val, const TX* x, TY* y, cudaStream_t s) {
     int launches = 0;
     int sm = p->sm_count > 0 ? p->sm_count : 152;
     if (p->nunits[DDF_BLAS] > 0) {
-        k_spmv<DDF_BLAS><<<grid_for(p->nunits[0], sm), DDF_CTA_THREADS, 0, s>>>(
-            p->cod, p->units[0], p->nunits[0], p->starts, p->col, p->val, x, y);
+        k_spmv<DDF_BLAS, TV, TX, TY, TA><<<grid_for(p->nunits[0], sm), DDF_CTA_THREADS, 0, s>>>(
+            p->cod, p->units[0], p->nunits[0], p->starts, p->col, val, x, y);
         ddf_count_launch();
         ++launches;
     }
     if (p->nunits[DDF_PSC1] > 0) {
-        k_spmv<DDF_PSC1><<<grid_for(p->nunits[1], sm), DDF_CTA_THREADS, 0, s>>>(
-            p->cod, p->units[1], p->nunits[1], p->starts, p->col, p->val, x, y);
+        k_spmv<DDF_PSC1, TV, TX, TY, TA><<<grid_for(p->nunits[1], sm), DDF_CTA_THREADS, 0, s>>>(
+            p->cod, p->units[1], p->nunits[1], p->starts, p->col, val, x, y);
         ddf_count_launch();
         ++launches;
     }
     if (p->nunits[DDF_PSC2] > 0) {
-        k_spmv<DDF_PSC2><<<grid_for(p->nunits[2], sm), DDF_CTA_THREADS, 0, s>>>(
-            p->cod, p->units[2], p->nunits[2], p->starts, p->col, p->val, x, y);
+        k_spmv<DDF_PSC2, TV, TX, TY, TA><<<grid_for(p->nunits[2], sm), DDF_CTA_THREADS, 0, s>>>(
+            p->cod, p->units[2], p->nunits[2], p->starts, p->col, val, x, y);
         ddf_count_launch();
         ++launches;
     }
-    p->last_launches = launches;
+    return launches;
+}
+
+}  // namespace
+
+ddf_status ddf_launch_spmv(ddf_plan_s* p, const double* x, double* y, cudaStream_t s) {
+    p->last_launches = launch_all<double, double, double, double>(p, p->val, x, y, s);
+    DDF_CUDA_TRY(cudaGetLastError());
+    return DDF_OK;
+}
+
+ddf_status ddf_launch_spmv_lp(ddf_plan_s* p, const void* x, void* y, int vec_dtype, cudaStream_t s) {
+    using bf = __nv_bfloat16;
+    int l = 0;
+    if (p->vdtype == DDF_F32 && vec_dtype == DDF_F32)
+        l = launch_all<float, float, float, float>(p, (const float*)p->val_lp, (const float*)x, (float*)y, s);
+    else if (p->vdtype == DDF_F32 && vec_dtype == DDF_BF16)
+        l = launch_all<float, bf, bf, float>(p, (const float*)p->val_lp, (const bf*)x, (bf*)y, s);
+    else if (p->vdtype == DDF_BF16 && vec_dtype == DDF_F32)
+        l = launch_all<bf, float, float, float>(p, (const bf*)p->val_lp, (const float*)x, (float*)y, s);
+    else if (p->vdtype == DDF_BF16 && vec_dtype == DDF_BF16)
+        l = launch_all<bf, bf, bf, float>(p, (const bf*)p->val_lp, (const bf*)x, (bf*)y, s);
+    else
+        return DDF_ERR_ARG;
+    p->last_launches = l;
     DDF_CUDA_TRY(cudaGetLastError());
     return DDF_OK;
 }
