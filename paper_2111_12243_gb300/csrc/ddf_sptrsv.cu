@@ -157,17 +157,39 @@ k_sptrsv(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64_t 
                 }
             }
             TX acc = 0;
-            if (act) {
-                typename B::U xv[SMAX];
+            // Read the dependencies held in registers; while some are not
+            // ready, one lane of the warp waits on its first missing value and
+            // the others re-read after it arrives, so a waiting warp costs one
+            // poller instead of one per lane.
+            typename B::U xv[SMAX];
 #pragma unroll
-                for (int k = 0; k < SMAX; ++k) xv[k] = jj[k] >= 0 ? B::ld(x + jj[k]) : (typename B::U)0;
+            for (int k = 0; k < SMAX; ++k) xv[k] = jj[k] >= 0 ? B::ld(x + jj[k]) : (typename B::U)0;
+            while (true) {
+                int miss = -1;
 #pragma unroll
-                for (int k = 0; k < SMAX; ++k) {
-                    if (jj[k] >= 0) {
-                        TX xd = (xv[k] != B::SENT) ? B::val(xv[k]) : wait_x<TX>(x + jj[k], status, abort_flag, cap_ns);
-                        acc += vv[k] * xd;
-                    }
+                for (int k = SMAX - 1; k >= 0; --k)
+                    if (jj[k] >= 0 && xv[k] == B::SENT) miss = k;
+                const unsigned pending = __ballot_sync(0xffffffffu, miss >= 0);
+                if (!pending) break;
+                if (lane == __ffs(pending) - 1) {
+                    TX w = wait_x<TX>(x + jj[miss], status, abort_flag, cap_ns);
+                    xv[miss] = B::bits(w) == B::SENT ? B::CANON : B::bits(w);
                 }
+                __syncwarp();
+                if (ddf_ld_relaxed_s32(abort_flag) != 0) {
+#pragma unroll
+                    for (int k = 0; k < SMAX; ++k)
+                        if (jj[k] >= 0 && xv[k] == B::SENT) xv[k] = B::CANON;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < SMAX; ++k)
+                        if (jj[k] >= 0 && xv[k] == B::SENT) xv[k] = B::ld(x + jj[k]);
+                }
+            }
+            if (act) {
+#pragma unroll
+                for (int k = 0; k < SMAX; ++k)
+                    if (jj[k] >= 0) acc += vv[k] * B::val(xv[k]);
                 for (int32_t i1 = li + SMAX * v; i1 < L; i1 += v) {
                     const int32_t j = (C.type == DDF_BLAS)   ? hb + C.sigma * i1
                                       : (C.type == DDF_PSC1) ? hb + (col[C.sref + i1] - C.h0)
