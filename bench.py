@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=256)
     return ap.parse_args()
 
 
@@ -244,12 +246,107 @@ def run_ours(args, rank, world, local_rank):
     mixed = None
     if not args.no_mixed:
         mixed = run_mixed(D, ddf, torch, stream, flush, breakdown)
+    batched = None
+    if not args.no_batch:
+        del D
+        torch.cuda.empty_cache()
+        batched = run_batch(args, ddf, torch, dev, stream, flush)
 
     return {
         "value": value, "ms_per_step": ms, "wall_s": wall, "launches": launches, "clocks": clk,
         "breakdown": breakdown, "roofline": roofline, "e2e": e2e, "exec_bytes_per_step": exec_b,
-        "mixed": mixed,
+        "mixed": mixed, "batched": batched,
     }
+
+
+def run_batch(args, ddf, torch, dev, stream, flush, nrhs=32, reps=5):
+    """The batching form: 256 uneven matrices (FP32 values), 32 right-hand
+    sides each.  Batched: one block-diagonal plan per kind, tiles picked by
+    ddf_tune, SpMM + SpTRSM recorded in one CUDA graph and replayed.  Compared
+    with per-matrix launches of the same multi-RHS executors and with the
+    plain path (the FP64 single-vector executors, one call per matrix and
+    right-hand side)."""
+    mats, rhs = synth.batch(args.batch_count, nrhs=nrhs)
+    lows = [synth.lower_triangle(m) for m in mats]
+    td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    A = [(td(m.rowptr), td(m.colidx), td(m.values), m.n_cols) for m in mats]
+    L = [(td(m.rowptr), td(m.colidx), td(m.values), m.n_cols) for m in lows]
+    N = sum(m.n_rows for m in mats)
+    X = td(np.concatenate(rhs))                     # [N][32] float32
+    Y = torch.empty((N, nrhs), dtype=torch.float32, device=dev)
+    Xs = torch.empty((N, nrhs), dtype=torch.float32, device=dev)
+    o32 = ddf.ddf_opts_default(store_dtype=ddf.DDF_F32)
+    pA = ddf.ddf_inspect_batch(A, ddf.DDF_SPMV, o32)
+    pL = ddf.ddf_inspect_batch(L, ddf.DDF_SPTRSV, o32)
+    tile_spmv = ddf.ddf_tune(pA, X, Y, nrhs)
+    tile_trsv = ddf.ddf_tune(pL, X, Xs, nrhs)
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(stream)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            ddf.ddf_spmm(pA, X, Y, nrhs, stream=side)
+            ddf.ddf_sptrsm(pL, X, Xs, nrhs, stream=side)
+    stream.wait_stream(side)
+
+    def timed(fn, r=reps):
+        ts = []
+        for _ in range(r):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    t_graph = timed(g.replay)
+    st_graph = ddf.ddf_get_status(pL)
+    sa, sl = ddf.ddf_plan_stats(pA), ddf.ddf_plan_stats(pL)
+    nnzA, nnzL = sa["points"], sl["points"]
+    # algorithmic bytes: FP32 values once, the 32-wide blocks read once and written once
+    bytes_spmm = 4 * nnzA + 4 * nrhs * (sa["n_cols"] + sa["n_rows"]) + 4 * sa["ops"][2] + 64 * sum(sa["ncodelets"])
+    bytes_trsm = 4 * nnzL + 4 * sl["n_rows"] + 4 * nrhs * 3 * sl["n_rows"] + 4 * sl["ops"][2] \
+        + 64 * sum(sl["ncodelets"])
+    # per-matrix launches of the same multi-RHS executors
+    pa = [ddf.ddf_inspect(*a[:3], a[3], ddf.DDF_SPMV, o32) for a in A]
+    pl = [ddf.ddf_inspect(*l[:3], l[3], ddf.DDF_SPTRSV, o32) for l in L]
+    offs = np.concatenate([[0], np.cumsum([m.n_rows for m in mats])])
+
+    def per_matrix():
+        for i in range(len(mats)):
+            a, b = int(offs[i]), int(offs[i + 1])
+            ddf.ddf_spmm(pa[i], X[a:b], Y[a:b], nrhs)
+            ddf.ddf_sptrsm(pl[i], X[a:b], Xs[a:b], nrhs)
+
+    t_per = timed(per_matrix, 3)
+    # the plain path: FP64 single-vector executors, one call per matrix and right-hand side
+    pa64 = [ddf.ddf_inspect(*a[:3], a[3], ddf.DDF_SPMV) for a in A]
+    pl64 = [ddf.ddf_inspect(*l[:3], l[3], ddf.DDF_SPTRSV) for l in L]
+    X64 = X.double().t().contiguous()                # [32][N]
+    Y64 = torch.empty_like(X64)
+    S64 = torch.empty_like(X64)
+
+    def plain():
+        for i in range(len(mats)):
+            a, b = int(offs[i]), int(offs[i + 1])
+            for k in range(nrhs):
+                ddf.ddf_spmv(pa64[i], X64[k, a:b], Y64[k, a:b])
+                ddf.ddf_sptrsv(pl64[i], X64[k, a:b], S64[k, a:b])
+
+    t_plain = timed(plain, 1)
+    err = float(torch.linalg.norm(Y.double().t() - Y64) / torch.linalg.norm(Y64))
+    errs = float(torch.linalg.norm(Xs.double().t() - S64) / torch.linalg.norm(S64))
+    for p in pa + pl + pa64 + pl64 + [pA, pL]:
+        p.destroy()
+    return {"matrices": len(mats), "rows": int(N), "nnz": int(nnzA), "nnz_lower": int(nnzL), "nrhs": nrhs,
+            "dtype": "f32 values and vectors, f32 sums", "tile_spmm_unit_nnz": tile_spmv,
+            "tile_sptrsm_units_per_cta": tile_trsv, "graph_ms": round(t_graph, 4), "graph_status": st_graph,
+            "graph_gbs": round((bytes_spmm + bytes_trsm) / (t_graph * 1e-3) / 1e9, 1),
+            "per_matrix_multi_rhs_ms": round(t_per, 3), "speedup_vs_per_matrix": round(t_per / t_graph, 2),
+            "plain_fp64_per_rhs_ms": round(t_plain, 2), "speedup_vs_plain_fp64": round(t_plain / t_graph, 2),
+            "spmm_relerr_vs_fp64": err, "sptrsm_relerr_vs_fp64": errs}
 
 
 def run_mixed(D, ddf, torch, stream, flush, breakdown, reps=5):
@@ -484,6 +581,7 @@ def main():
             "clocks": r["clocks"],
             "breakdown": r["breakdown"],
             "mixed_precision": r["mixed"],
+            "batched": r["batched"],
             "exec_bytes_per_step": r["exec_bytes_per_step"],
         }
         print(json.dumps(line))

@@ -187,6 +187,47 @@ DDF_API ddf_status ddf_spmv_lowp(ddf_plan_t p, const void* x, void* y, ddf_dtype
 DDF_API ddf_status ddf_sptrsv_refine(ddf_plan_t p, const double* b, double* x, double tol, int32_t max_iter,
                                      ddf_stream_t s, int32_t* iters, double* relres);
 
+/*
+ * Batched inspection: `count` independent matrices (each a ddf_csr as for
+ * ddf_inspect, host or device arrays, possibly of different sizes) are
+ * inspected as one block-diagonal matrix.  Matrix i occupies rows and columns
+ * starting at the sum of the sizes of matrices 0..i-1; multi-RHS vectors of
+ * the batch are laid out the same way.  For DDF_SPTRSV every matrix must be
+ * square and lower triangular; the level sets then mix rows of all matrices,
+ * which widens every level.  Everything else is as in ddf_inspect.
+ */
+DDF_API ddf_status ddf_inspect_batch(const ddf_csr* mats, int32_t count, ddf_kind kind, const ddf_opts* o,
+                                     ddf_stream_t s, ddf_plan_t* out);
+
+/*
+ * Multi-RHS SpMV: Y = A X for nrhs (1..32) right-hand sides.  X is
+ * [n_cols][nrhs] and Y [n_rows][nrhs], row-major, device memory, of dtype
+ * DDF_F64 (FP64 values and sums) or DDF_F32 (the plan's FP32 values, FP32
+ * sums; the plan needs store_dtype DDF_F32).  One warp runs one row at a
+ * time, lane k accumulating right-hand side k, so no reduction is needed.
+ */
+DDF_API ddf_status ddf_spmm(ddf_plan_t p, const void* X, void* Y, int32_t nrhs, ddf_dtype dtype, ddf_stream_t s);
+
+/*
+ * Multi-RHS SpTRSV: solves L X = B for nrhs (1..32) right-hand sides, layouts
+ * and dtypes as in ddf_spmm (B and X must not overlap).  Same level-ordered
+ * codelets and per-element ready flags as ddf_sptrsv; the work of one
+ * dependency hop is nrhs rows of work instead of one.  Plain launches only
+ * (no cooperative launch), so the call can be recorded in a CUDA graph.
+ */
+DDF_API ddf_status ddf_sptrsm(ddf_plan_t p, const void* B, void* X, int32_t nrhs, ddf_dtype dtype,
+                              ddf_stream_t s);
+
+/*
+ * Autotuner for the multi-RHS executors: rebuilds the plan's work units for
+ * each candidate tile size (target nonzeros per unit), times ddf_spmm (kind
+ * DDF_SPMV) or ddf_sptrsm (DDF_SPTRSV) on the given operands with CUDA events,
+ * and keeps the fastest.  *best_unit_nnz receives the choice (may be NULL).
+ * Overwrites the output operand.  Synchronises s.
+ */
+DDF_API ddf_status ddf_tune(ddf_plan_t p, const void* in, void* out, int32_t nrhs, ddf_dtype dtype,
+                            ddf_stream_t s, int32_t* best_unit_nnz);
+
 /* Synchronise s, then return and clear the plan's device status word. */
 DDF_API ddf_status ddf_get_status(ddf_plan_t p, ddf_stream_t s);
 
@@ -207,6 +248,22 @@ DDF_API ddf_status ddf_plan_stats(ddf_plan_t p, ddf_plan_stats_t* st);
  */
 DDF_API ddf_status ddf_plan_export(ddf_plan_t p, int64_t* records, int64_t* ncodelets, int32_t* seq,
                            int32_t* part_ptr, int32_t* depth, int64_t* gs);
+
+/*
+ * Plan serialisation (reuse of an inspection across runs, the amortisation
+ * of Sec. V-C).  ddf_plan_save with buf == NULL stores the required size in
+ * *len; otherwise it writes the plan (descriptors, work units, level order,
+ * the plan's copies of indices and values, low-precision copies) into buf,
+ * which must hold *len >= that size bytes, and returns DDF_ERR_ARG with the
+ * size in *len when it is too small.  ddf_plan_load rebuilds a device plan
+ * on the current device from such a buffer without re-inspection; it checks
+ * the header, the sizes and a checksum and returns DDF_ERR_ARG on any
+ * mismatch.  The buffer is host-endian.  Both synchronise (save: the plan's
+ * stream; load: s).  Load buffers only from ddf_plan_save: the checksum
+ * detects corruption, not tampering.
+ */
+DDF_API ddf_status ddf_plan_save(ddf_plan_t p, void* buf, size_t* len);
+DDF_API ddf_status ddf_plan_load(const void* buf, size_t len, ddf_stream_t s, ddf_plan_t* out);
 
 /* Release every device buffer of the plan (stream-ordered on the stream the
  * plan was inspected on).  NULL is ignored. */

@@ -34,7 +34,8 @@ RECORD_FIELDS = ("part", "type", "q0", "m", "n", "f_str", "rho", "g_str", "gamma
 EXPORTS = ("ddf_opts_default", "ddf_inspect", "ddf_update_values", "ddf_spmv", "ddf_sptrsv",
            "ddf_get_status", "ddf_plan_stats", "ddf_plan_export", "ddf_plan_destroy",
            "ddf_status_string", "ddf_last_launches", "ddf_kernel_launches",
-           "ddf_debug_set_dependency", "ddf_sptrsv_csr_noalloc", "ddf_spmv_lowp", "ddf_sptrsv_refine")
+           "ddf_debug_set_dependency", "ddf_sptrsv_csr_noalloc", "ddf_spmv_lowp", "ddf_sptrsv_refine",
+           "ddf_inspect_batch", "ddf_spmm", "ddf_sptrsm", "ddf_tune", "ddf_plan_save", "ddf_plan_load")
 #: rows accepted by ddf_sptrsv_csr_noalloc (the size of its static scratch)
 DDF_NOALLOC_MAX_ROWS = 1 << 20
 
@@ -107,6 +108,19 @@ def lib():
         L.ddf_sptrsv_refine.argtypes = [P, P, P, ctypes.c_double, I32, P, ctypes.POINTER(I32),
                                         ctypes.POINTER(ctypes.c_double)]
         L.ddf_sptrsv_refine.restype = ctypes.c_int
+        L.ddf_inspect_batch.argtypes = [ctypes.POINTER(ddf_csr), I32, ctypes.c_int, ctypes.POINTER(ddf_opts), P,
+                                        ctypes.POINTER(P)]
+        L.ddf_inspect_batch.restype = ctypes.c_int
+        L.ddf_spmm.argtypes = [P, P, P, I32, ctypes.c_int, P]
+        L.ddf_spmm.restype = ctypes.c_int
+        L.ddf_sptrsm.argtypes = [P, P, P, I32, ctypes.c_int, P]
+        L.ddf_sptrsm.restype = ctypes.c_int
+        L.ddf_tune.argtypes = [P, P, P, I32, ctypes.c_int, P, ctypes.POINTER(I32)]
+        L.ddf_tune.restype = ctypes.c_int
+        L.ddf_plan_save.argtypes = [P, P, ctypes.POINTER(ctypes.c_size_t)]
+        L.ddf_plan_save.restype = ctypes.c_int
+        L.ddf_plan_load.argtypes = [P, ctypes.c_size_t, P, ctypes.POINTER(P)]
+        L.ddf_plan_load.restype = ctypes.c_int
         L.ddf_sptrsv_csr_noalloc.argtypes = [I32, I64, P, P, P, P, P, I64, P]
         L.ddf_sptrsv_csr_noalloc.restype = ctypes.c_int
         for name in ("ddf_inspect", "ddf_update_values", "ddf_spmv", "ddf_sptrsv", "ddf_get_status",
@@ -253,6 +267,82 @@ def ddf_sptrsv_refine(plan: Plan, b, x, tol: float = 1e-12, max_iter: int = 20, 
     st = lib().ddf_sptrsv_refine(plan.handle, _dev_vec(b, plan.n_rows, "b"), _dev_vec(x, plan.n_rows, "x"),
                                  float(tol), int(max_iter), _stream(stream), ctypes.byref(it), ctypes.byref(rr))
     return int(st), int(it.value), float(rr.value)
+
+
+def ddf_inspect_batch(mats, kind: int, opts: ddf_opts | None = None, stream=None) -> Plan:
+    """Inspect a list of (rowptr, colidx, values, n_cols) CSR tuples as one
+    block-diagonal matrix (tensors on the device or host arrays)."""
+    arr = (ddf_csr * len(mats))()
+    keep = []
+    n_rows = n_cols = 0
+    for i, (rp, ci, va, nc) in enumerate(mats):
+        prp, dr, k1 = _ptr(rp, np.int32)
+        pci, dc, k2 = _ptr(ci, np.int32)
+        pva, dv, k3 = _ptr(va, np.float64)
+        keep += [k1, k2, k3]
+        arr[i] = ddf_csr(int(len(rp)) - 1, int(nc), int(len(ci)), prp, pci, pva, dr, 0)
+        n_rows += int(len(rp)) - 1
+        n_cols += int(nc)
+    h = ctypes.c_void_p()
+    st = lib().ddf_inspect_batch(arr, len(mats), int(kind), ctypes.byref(opts) if opts is not None else None,
+                                 _stream(stream), ctypes.byref(h))
+    del keep
+    _check(st, "ddf_inspect_batch")
+    return Plan(h, int(kind), n_rows, n_cols)
+
+
+def _mat(t, rows, nrhs, name):
+    import torch
+    if not (hasattr(t, "is_cuda") and t.is_cuda) or t.dtype not in (torch.float64, torch.float32) \
+            or not t.is_contiguous() or t.numel() != rows * nrhs:
+        raise ValueError(f"{name} must be a contiguous float64/float32 CUDA tensor of {rows} x {nrhs}")
+    return ctypes.c_void_p(t.data_ptr()), (DDF_F64 if t.dtype == torch.float64 else DDF_F32)
+
+
+def ddf_spmm(plan: Plan, X, Y, nrhs: int, stream=None):
+    """Y = A X for nrhs right-hand sides (row-major [n][nrhs] CUDA tensors)."""
+    px, dx = _mat(X, plan.n_cols, nrhs, "X")
+    py, dy = _mat(Y, plan.n_rows, nrhs, "Y")
+    if dx != dy:
+        raise ValueError("X and Y must have the same dtype")
+    _check(lib().ddf_spmm(plan.handle, px, py, int(nrhs), dx, _stream(stream)), "ddf_spmm")
+
+
+def ddf_sptrsm(plan: Plan, B, X, nrhs: int, stream=None):
+    """Solve L X = B for nrhs right-hand sides (row-major [n][nrhs] CUDA tensors)."""
+    pb, db = _mat(B, plan.n_rows, nrhs, "B")
+    px, dx = _mat(X, plan.n_rows, nrhs, "X")
+    if db != dx:
+        raise ValueError("B and X must have the same dtype")
+    _check(lib().ddf_sptrsm(plan.handle, pb, px, int(nrhs), db, _stream(stream)), "ddf_sptrsm")
+
+
+def ddf_tune(plan: Plan, inp, out, nrhs: int, stream=None) -> int:
+    """Pick the multi-RHS tile size of a plan by timing candidates; returns it."""
+    rows_in = plan.n_cols if plan.kind == DDF_SPMV else plan.n_rows
+    pi, di = _mat(inp, rows_in, nrhs, "in")
+    po, do = _mat(out, plan.n_rows, nrhs, "out")
+    best = ctypes.c_int32(0)
+    _check(lib().ddf_tune(plan.handle, pi, po, int(nrhs), di, _stream(stream), ctypes.byref(best)), "ddf_tune")
+    return int(best.value)
+
+
+def ddf_plan_save(plan: Plan) -> bytes:
+    """Serialise a plan into bytes (reload it with ddf_plan_load)."""
+    L = lib()
+    n = ctypes.c_size_t(0)
+    _check(L.ddf_plan_save(plan.handle, None, ctypes.byref(n)), "ddf_plan_save")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(L.ddf_plan_save(plan.handle, buf, ctypes.byref(n)), "ddf_plan_save")
+    return buf.raw[:n.value]
+
+
+def ddf_plan_load(data: bytes, n_rows: int, n_cols: int, kind: int, stream=None) -> Plan:
+    """Rebuild a device plan from ddf_plan_save's bytes, without re-inspection."""
+    h = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(bytes(data), len(data))
+    _check(lib().ddf_plan_load(buf, len(data), _stream(stream), ctypes.byref(h)), "ddf_plan_load")
+    return Plan(h, int(kind), int(n_rows), int(n_cols))
 
 
 def ddf_get_status(plan: Plan, stream=None) -> int:

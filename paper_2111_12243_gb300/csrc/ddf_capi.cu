@@ -78,6 +78,95 @@ __global__ void k_check_diag(int32_t n, const int32_t* __restrict__ rp, const do
 
 }  // namespace
 
+// A plan shell: options checked, status words allocated, nothing inspected.
+ddf_status ddf_new_plan(ddf_kind kind, const ddf_opts* o, cudaStream_t s, int32_t n, int32_t n_cols, int64_t nnz,
+                        ddf_plan_s** out) {
+    *out = nullptr;
+    ddf_opts opts;
+    if (o) opts = *o;
+    else ddf_opts_default(&opts);
+    ddf_status st = check_opts(&opts);
+    if (st) return st;
+    ddf_plan_s* p = new (std::nothrow) ddf_plan_s();
+    if (!p) return DDF_ERR_OOM;
+    memset(p, 0, sizeof(*p));
+    p->kind = kind;
+    p->opts = opts;
+    p->stream = s;
+    p->n = n;
+    p->n_cols = n_cols;
+    p->nnz = nnz;
+    p->units_per_cta = DDF_WARPS_PER_CTA;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete p;
+        return DDF_ERR_CUDA;
+    }
+    (void)cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
+    init_pool_once(p->device);
+    st = ddf_alloc(&p->status, 1, s);
+    if (!st) st = ddf_alloc(&p->ticket, 2, s);
+    if (!st && (cudaMemsetAsync(p->status, 0, sizeof(int32_t), s) != cudaSuccess ||
+                cudaMemsetAsync(p->ticket, 0, 2 * sizeof(uint32_t), s) != cudaSuccess)) {
+        (void)cudaGetLastError();
+        st = DDF_ERR_CUDA;
+    }
+    if (st) {
+        release(p);
+        delete p;
+        return st;
+    }
+    *out = p;
+    return DDF_OK;
+}
+
+// Inspect device CSR arrays the plan takes over (rp, ci and, when present, v);
+// on error everything is released and *out stays NULL.
+ddf_status ddf_finish_plan(ddf_plan_s* p, int32_t* rp, int32_t* ci, double* v, cudaStream_t s, ddf_plan_t* out) {
+    const ddf_kind kind = p->kind;
+    ddf_status st = DDF_OK;
+    if (kind == DDF_SPMV && p->nnz > 0 && v == nullptr) {
+        // values come later through ddf_update_values: reserve them now
+        st = ddf_alloc(&v, p->nnz, s);
+        if (!st) {
+            st = ddf_build_plan(p, rp, ci, nullptr, s);
+            if (!st) {
+                p->val = v;
+                v = nullptr;
+            }
+        }
+    } else {
+        st = ddf_build_plan(p, rp, ci, v, s);
+    }
+    if (kind == DDF_SPMV) {
+        // on success the plan adopted rp / ci / v as its own arrays
+        if (st) {
+            p->starts = nullptr;
+            p->col = nullptr;
+            p->val = nullptr;
+            ddf_free(rp, s);
+            ddf_free(ci, s);
+            ddf_free(v, s);
+        }
+    } else {
+        // SpTRSV keeps rowptr (as orig_rowptr) and drops the CSR copies
+        if (p->orig_rowptr != rp) ddf_free(rp, s);
+        ddf_free(ci, s);
+        ddf_free(v, s);
+    }
+    if (!st) st = ddf_make_lowp(p, s);
+    if (!st && cudaStreamSynchronize(s) != cudaSuccess) st = DDF_ERR_CUDA;
+    if (st) {
+        release(p);
+        (void)cudaStreamSynchronize(s);
+        (void)cudaGetLastError();
+        delete p;
+        return st;
+    }
+    *out = p;
+    return DDF_OK;
+}
+
 extern "C" {
 
 void ddf_opts_default(ddf_opts* o) {
@@ -120,89 +209,35 @@ ddf_status ddf_inspect(const ddf_csr* A, ddf_kind kind, const ddf_opts* o, ddf_s
     if (A->n_rows < 0 || A->n_cols < 0 || A->nnz < 0 || A->nnz > 0x7fffffffll) return DDF_ERR_ARG;
     if (!A->rowptr || (A->nnz > 0 && !A->colidx)) return DDF_ERR_ARG;
     if (kind == DDF_SPTRSV && A->n_rows != A->n_cols) return DDF_ERR_NOT_SQUARE;
-    ddf_opts opts;
-    if (o) opts = *o;
-    else ddf_opts_default(&opts);
-    ddf_status st = check_opts(&opts);
-    if (st) return st;
+    {
+        ddf_opts opts;
+        if (o) opts = *o;
+        else ddf_opts_default(&opts);
+        ddf_status sto = check_opts(&opts);
+        if (sto) return sto;
+    }
     if (!A->on_device) {
         // host CSR: cheap structural checks before any device work
         if (A->rowptr[0] != 0 || (int64_t)A->rowptr[A->n_rows] != A->nnz) return DDF_ERR_UNSORTED;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    ddf_plan_s* p = new (std::nothrow) ddf_plan_s();
-    if (!p) return DDF_ERR_OOM;
-    memset(p, 0, sizeof(*p));
-    p->kind = kind;
-    p->opts = opts;
-    p->stream = s;
-    p->n = A->n_rows;
-    p->n_cols = A->n_cols;
-    p->nnz = A->nnz;
-    p->units_per_cta = DDF_WARPS_PER_CTA;
-    if (cudaGetDevice(&p->device) != cudaSuccess) {
-        (void)cudaGetLastError();
-        delete p;
-        return DDF_ERR_CUDA;
-    }
-    (void)cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
-    init_pool_once(p->device);
-
+    ddf_plan_s* p = nullptr;
+    ddf_status st = ddf_new_plan(kind, o, s, A->n_rows, A->n_cols, A->nnz, &p);
+    if (st) return st;
     int32_t* rp = nullptr;
     int32_t* ci = nullptr;
     double* v = nullptr;
     st = stage(&rp, A->rowptr, (int64_t)A->n_rows + 1, A->on_device, s);
     if (!st) st = stage(&ci, A->colidx, A->nnz, A->on_device, s);
     if (!st && A->values) st = stage(&v, A->values, A->nnz, A->on_device, s);
-    if (!st) st = ddf_alloc(&p->status, 1, s);
-    if (!st) st = ddf_alloc(&p->ticket, 2, s);
-    if (!st) {
-        if (cudaMemsetAsync(p->status, 0, sizeof(int32_t), s) != cudaSuccess ||
-            cudaMemsetAsync(p->ticket, 0, 2 * sizeof(uint32_t), s) != cudaSuccess) {
-            (void)cudaGetLastError();
-            st = DDF_ERR_CUDA;
-        }
-    }
-    if (!st && kind == DDF_SPMV && A->nnz > 0 && v == nullptr) {
-        // values come later through ddf_update_values: reserve them now
-        st = ddf_alloc(&v, A->nnz, s);
-        if (!st) {
-            st = ddf_build_plan(p, rp, ci, nullptr, s);
-            if (!st) {
-                p->val = v;
-                v = nullptr;
-            }
-        }
-    } else if (!st) {
-        st = ddf_build_plan(p, rp, ci, v, s);
-    }
-    if (kind == DDF_SPMV) {
-        // on success the plan adopted rp / ci / v as its own arrays
-        if (st) {
-            p->starts = nullptr;
-            p->col = nullptr;
-            p->val = nullptr;
-            ddf_free(rp, s);
-            ddf_free(ci, s);
-            ddf_free(v, s);
-        }
-    } else {
-        // SpTRSV keeps rowptr (as orig_rowptr) and drops the CSR copies
-        if (p->orig_rowptr != rp) ddf_free(rp, s);
+    if (st) {
+        ddf_free(rp, s);
         ddf_free(ci, s);
         ddf_free(v, s);
-    }
-    if (!st) st = ddf_make_lowp(p, s);
-    if (!st && cudaStreamSynchronize(s) != cudaSuccess) st = DDF_ERR_CUDA;
-    if (st) {
-        release(p);
-        (void)cudaStreamSynchronize(s);
-        (void)cudaGetLastError();
-        delete p;
+        ddf_plan_destroy(p);
         return st;
     }
-    *out = p;
-    return DDF_OK;
+    return ddf_finish_plan(p, rp, ci, v, s, out);
 }
 
 ddf_status ddf_update_values(ddf_plan_t p, const double* values, int32_t on_device, ddf_stream_t stream) {

@@ -1046,6 +1046,23 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
     DDF_CUDA_TRY(cudaGetLastError());
 
     // executor units
+    TRY(ddf_build_units(p, s));
+    p->stats_ready = 0;
+    DDF_CUDA_TRY(cudaStreamSynchronize(s));
+    return DDF_OK;
+}
+
+// (Re)build the executor work units of a plan from its codelets with the
+// plan's current unit_nnz (SpMV: one list per codelet type; SpTRSV: one list
+// in level order).
+ddf_status ddf_build_units(ddf_plan_s* p, cudaStream_t s) {
+    Scratch tmp{s, {}};
+    const int kind = p->kind;
+    const int64_t ncod = p->ncod;
+    for (int k = 0; k < 3; ++k) {
+        ddf_free(p->units[k], s);
+        p->nunits[k] = 0;
+    }
     int split = kind == DDF_SPMV;
     int32_t *c0 = nullptr, *c1 = nullptr, *c2 = nullptr;
     int64_t *o0 = nullptr, *o1 = nullptr, *o2 = nullptr;
@@ -1085,8 +1102,6 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
     }
     DDF_CUDA_TRY(cudaGetLastError());
 
-    p->stats_ready = 0;
-    DDF_CUDA_TRY(cudaStreamSynchronize(s));
     return DDF_OK;
 }
 

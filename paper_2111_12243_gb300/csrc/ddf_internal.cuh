@@ -156,6 +156,11 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
                           const double* values, cudaStream_t s);
 ddf_status ddf_gather_values(ddf_plan_s* p, const double* values, cudaStream_t s);
 ddf_status ddf_compute_stats(ddf_plan_s* p);
+ddf_status ddf_build_units(ddf_plan_s* p, cudaStream_t s);
+// ddf_capi.cu
+ddf_status ddf_new_plan(ddf_kind kind, const ddf_opts* o, cudaStream_t s, int32_t n, int32_t n_cols, int64_t nnz,
+                        ddf_plan_s** out);
+ddf_status ddf_finish_plan(ddf_plan_s* p, int32_t* rp, int32_t* ci, double* v, cudaStream_t s, ddf_plan_t* out);
 // ddf_spmv.cu
 ddf_status ddf_launch_spmv(ddf_plan_s* p, const double* x, double* y, cudaStream_t s);
 ddf_status ddf_launch_spmv_lp(ddf_plan_s* p, const void* x, void* y, int vec_dtype, cudaStream_t s);

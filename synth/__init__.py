@@ -17,4 +17,6 @@ from .matrices import (  # noqa: F401
     uniform_vector,
     workload,
     WORKLOADS,
+    batch,
+    batch_member,
 )

@@ -358,3 +358,69 @@ def workload(name: str, scale: float = 1.0):
     x = uniform_vector(a.n_cols, seed)
     b = uniform_vector(a.n_rows, seed + 1000)
     return a, lo, x, b
+
+
+# ----------------------------------------------------------------------------
+# batch of uneven matrices (many small systems with many right-hand sides)
+# ----------------------------------------------------------------------------
+
+def _star(dims, radius):
+    """Offsets of a star stencil: the centre and +-1..radius along each axis."""
+    offs = [(0, 0, 0)]
+    for ax in range(len(dims)):
+        for r in range(1, radius + 1):
+            for sgn in (-1, 1):
+                o = [0, 0, 0]
+                o[ax] = sgn * r
+                offs.append(tuple(o))
+    return offs
+
+
+def _f32_dominant(rowptr, colidx, rng):
+    """N(0,1) off-diagonals and a diagonal of 1 + sum(|row|), all exactly
+    representable in FP32."""
+    nnz = colidx.size
+    v = rng.standard_normal(nnz).astype(np.float32).astype(np.float64)
+    v = _dominant_diagonal(rowptr, colidx, v)
+    return v.astype(np.float32).astype(np.float64)
+
+
+def batch_member(n_target: int, kind: str, seed: int) -> CSR:
+    """One matrix of the batch: a 2-D star stencil of radius 3 (13 points), a
+    3-D star stencil of radius 2 (13 points) or a power-law pattern with mean
+    row length 12; FP32-exact N(0,1) values made diagonally dominant."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if kind == "2d":
+        k = max(4, int(round(n_target ** 0.5)))
+        dims = (k, max(4, n_target // k), 1)
+        rowptr, colidx, _, _ = _stencil_pattern(dims, _star(dims[:2], 3))
+        n = dims[0] * dims[1]
+    elif kind == "3d":
+        k = max(4, int(round(n_target ** (1.0 / 3.0))))
+        dims = (k, k, max(4, n_target // (k * k)))
+        rowptr, colidx, _, _ = _stencil_pattern(dims, _star(dims, 2))
+        n = dims[0] * dims[1] * dims[2]
+    else:
+        a = powerlaw(n_target, seed=seed, scale=1.9, max_len=2000)
+        v = _f32_dominant(a.rowptr.astype(np.int64), a.colidx, rng)
+        return CSR(a.n_rows, a.n_cols, a.rowptr, a.colidx, v)
+    rowptr = rowptr.astype(np.int64)
+    v = _f32_dominant(rowptr, colidx, rng)
+    return CSR(n, n, _check_int32(rowptr), colidx, v)
+
+
+def batch(count: int = 256, n_min: int = 1000, n_max: int = 200000, nrhs: int = 32,
+          seed: int = SEED_BASE + 5):
+    """(matrices, right-hand sides): ``count`` matrices with n log-uniform in
+    [n_min, n_max], each a random 2-D / 3-D star stencil or power-law pattern,
+    and for each an (n x nrhs) row-major float32 block of U[-1, 1] right-hand sides."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = np.exp(rng.uniform(np.log(n_min), np.log(n_max), count)).astype(np.int64)
+    kinds = rng.choice(["2d", "3d", "powerlaw"], size=count)
+    mats, rhs = [], []
+    for i in range(count):
+        m = batch_member(int(sizes[i]), str(kinds[i]), seed * 1000 + i)
+        mats.append(m)
+        rhs.append(np.random.Generator(np.random.PCG64(seed + 7 + i))
+                   .uniform(-1.0, 1.0, (m.n_rows, nrhs)).astype(np.float32))
+    return mats, rhs

@@ -1,0 +1,183 @@
+"""GPU checks of the batched and multi-RHS forms against the FP64 oracle.
+
+A batch is inspected as its block-diagonal matrix, so its plan must equal the
+oracle's Algorithm 1 on that matrix bit for bit.  Multi-RHS results are
+checked column by column against the oracle's single-vector SpMV and forward
+substitution.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+import paper_2111_12243_gb300 as ddf
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2111_12243_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def block_diag(mats):
+    rp = [np.zeros(1, np.int64)]
+    ci, va = [], []
+    r = c = z = 0
+    for m in mats:
+        rp.append(m.rowptr[1:].astype(np.int64) + z)
+        ci.append(m.colidx.astype(np.int64) + c)
+        va.append(m.values)
+        r += m.n_rows
+        c += m.n_cols
+        z += m.nnz
+    return synth.CSR(r, c, np.concatenate(rp).astype(np.int32), np.concatenate(ci).astype(np.int32),
+                     np.concatenate(va))
+
+
+@pytest.fixture(scope="module")
+def small_batch():
+    kinds = ["2d", "3d", "powerlaw", "3d", "2d", "powerlaw", "2d"]
+    sizes = [1000, 1500, 1200, 2500, 900, 3000, 1100]
+    return [synth.batch_member(n, k, 100 + i) for i, (n, k) in enumerate(zip(sizes, kinds))]
+
+
+def batch_plan(mats, kind, on_device=True, **opts):
+    tup = [((dev(m.rowptr), dev(m.colidx), dev(m.values)) if on_device else (m.rowptr, m.colidx, m.values))
+           + (m.n_cols,) for m in mats]
+    return ddf.ddf_inspect_batch(tup, kind, ddf.ddf_opts_default(**opts))
+
+
+@pytest.mark.parametrize("on_device", [True, False])
+def test_batch_plans_equal_block_diagonal_inspection(small_batch, on_device):
+    lows = [synth.lower_triangle(m) for m in small_batch]
+    for mats, kind, okind in ((small_batch, ddf.DDF_SPMV, oracle.SPMV), (lows, ddf.DDF_SPTRSV, oracle.SPTRSV)):
+        p = batch_plan(mats, kind, on_device)
+        got = ddf.ddf_plan_export(p)
+        bd = block_diag(mats)
+        ref = oracle.inspect(bd, okind)
+        assert np.array_equal(got["seq"], ref.perm)
+        assert np.array_equal(got["part_ptr"], ref.level_ptr)
+        assert np.array_equal(got["records"], ref.records)
+        assert oracle.check_plan(bd, okind, got["seq"], got["part_ptr"], got["gs"], got["records"]) == (0, -1)
+
+
+@pytest.mark.parametrize("nrhs", [1, 5, 32])
+def test_spmm_and_sptrsm_f64(small_batch, nrhs):
+    bd = block_diag(small_batch)
+    lo = block_diag([synth.lower_triangle(m) for m in small_batch])
+    rng = np.random.default_rng(nrhs)
+    X = rng.uniform(-1, 1, (bd.n_cols, nrhs))
+    B = rng.uniform(-1, 1, (lo.n_rows, nrhs))
+    p = batch_plan(small_batch, ddf.DDF_SPMV)
+    Y = torch.full((bd.n_rows, nrhs), float("nan"), dtype=torch.float64, device="cuda")
+    ddf.ddf_spmm(p, dev(X), Y, nrhs)
+    Yh = Y.cpu().numpy()
+    q = batch_plan([synth.lower_triangle(m) for m in small_batch], ddf.DDF_SPTRSV)
+    Xs = torch.zeros((lo.n_rows, nrhs), dtype=torch.float64, device="cuda")
+    ddf.ddf_sptrsm(q, dev(B), Xs, nrhs)
+    assert ddf.ddf_get_status(q) == 0
+    Xh = Xs.cpu().numpy()
+    for k in range(nrhs):
+        ry = oracle.spmv(bd, X[:, k])
+        assert np.linalg.norm(Yh[:, k] - ry) <= TOL * np.linalg.norm(ry)
+        rx = oracle.sptrsv(lo, B[:, k])
+        assert np.linalg.norm(Xh[:, k] - rx) <= TOL * np.linalg.norm(rx)
+
+
+def test_spmm_and_sptrsm_f32(small_batch):
+    nrhs = 32
+    bd = block_diag(small_batch)
+    lo = block_diag([synth.lower_triangle(m) for m in small_batch])
+    rng = np.random.default_rng(7)
+    X = rng.uniform(-1, 1, (bd.n_cols, nrhs)).astype(np.float32)
+    B = rng.uniform(-1, 1, (lo.n_rows, nrhs)).astype(np.float32)
+    p = batch_plan(small_batch, ddf.DDF_SPMV, store_dtype=ddf.DDF_F32)
+    Y = torch.empty((bd.n_rows, nrhs), dtype=torch.float32, device="cuda")
+    ddf.ddf_spmm(p, dev(X), Y, nrhs)
+    Yh = Y.double().cpu().numpy()
+    absa = synth.CSR(bd.n_rows, bd.n_cols, bd.rowptr, bd.colidx, np.abs(bd.values))
+    k_row = np.maximum(np.diff(bd.rowptr), 1)
+    for k in range(0, nrhs, 7):
+        xk = X[:, k].astype(np.float64)
+        ref = oracle.spmv(bd, xk)                       # batch values are exact in FP32
+        bound = 2 * k_row * U32 * oracle.spmv(absa, np.abs(xk)) + 1e-30
+        assert np.all(np.abs(Yh[:, k] - ref) <= bound)
+    q = batch_plan([synth.lower_triangle(m) for m in small_batch], ddf.DDF_SPTRSV, store_dtype=ddf.DDF_F32)
+    Xs = torch.zeros((lo.n_rows, nrhs), dtype=torch.float32, device="cuda")
+    ddf.ddf_sptrsm(q, dev(B), Xs, nrhs)
+    assert ddf.ddf_get_status(q) == 0
+    Xh = Xs.double().cpu().numpy()
+    for k in range(0, nrhs, 5):
+        bk = B[:, k].astype(np.float64)
+        r = bk - oracle.spmv(lo, Xh[:, k])
+        assert np.linalg.norm(r) <= 1e-5 * np.linalg.norm(bk)
+
+
+def test_tune_and_graph_capture(small_batch):
+    nrhs = 32
+    bd = block_diag(small_batch)
+    lows = [synth.lower_triangle(m) for m in small_batch]
+    lo = block_diag(lows)
+    rng = np.random.default_rng(3)
+    X = dev(rng.uniform(-1, 1, (bd.n_cols, nrhs)).astype(np.float32))
+    B = dev(rng.uniform(-1, 1, (lo.n_rows, nrhs)).astype(np.float32))
+    p = batch_plan(small_batch, ddf.DDF_SPMV, store_dtype=ddf.DDF_F32)
+    q = batch_plan(lows, ddf.DDF_SPTRSV, store_dtype=ddf.DDF_F32)
+    Y = torch.empty((bd.n_rows, nrhs), dtype=torch.float32, device="cuda")
+    Xs = torch.empty((lo.n_rows, nrhs), dtype=torch.float32, device="cuda")
+    assert ddf.ddf_tune(p, X, Y, nrhs) in (64, 128, 256, 512, 1024, 2048)
+    assert ddf.ddf_tune(q, B, Xs, nrhs) in (8, 16, 32, 64)
+    ddf.ddf_spmm(p, X, Y, nrhs)
+    ddf.ddf_sptrsm(q, B, Xs, nrhs)
+    torch.cuda.synchronize()
+    y0, x0 = Y.clone(), Xs.clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            ddf.ddf_spmm(p, X, Y, nrhs, stream=s)
+            ddf.ddf_sptrsm(q, B, Xs, nrhs, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(2):
+        Y.zero_()
+        Xs.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(Y, y0)
+        assert torch.equal(Xs, x0)
+    assert ddf.ddf_get_status(q) == 0
+
+
+def test_multi_rhs_argument_errors(small_batch):
+    p = batch_plan(small_batch[:2], ddf.DDF_SPMV)
+    n = p.n_rows
+    X = torch.zeros((p.n_cols, 33), dtype=torch.float64, device="cuda")
+    Y = torch.zeros((n, 33), dtype=torch.float64, device="cuda")
+    with pytest.raises(ddf.DDFError):
+        ddf.ddf_spmm(p, X, Y, 33)
+    Xf = torch.zeros((p.n_cols, 4), dtype=torch.float32, device="cuda")
+    Yf = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(ddf.DDFError) as e:
+        ddf.ddf_spmm(p, Xf, Yf, 4)                         # FP64-only plan
+    assert e.value.status == 1
+    with pytest.raises(ddf.DDFError) as e:
+        ddf.ddf_sptrsm(p, Xf, Yf, 4)
+    assert e.value.status in (1, 8)
+    bad = synth.CSR(2, 3, np.array([0, 1, 2], np.int32), np.array([0, 1], np.int32), np.ones(2))
+    with pytest.raises(ddf.DDFError) as e:
+        ddf.ddf_inspect_batch([(bad.rowptr, bad.colidx, bad.values, 3)], ddf.DDF_SPTRSV)
+    assert e.value.status == 2
