@@ -63,9 +63,11 @@ def _L():
         lib.ora_levels.argtypes = [i32, P, P, P]
         lib.ora_levels.restype = i32
         lib.ora_level_order.argtypes = [i32, P, i32, P, P]
+        lib.ora_coarse_order.argtypes = [i32, P, i32, i32, P, P, P]
+        lib.ora_check_schedule.argtypes = [i32, P, P, P, P, i32, P]
         lib.ora_codelet_cost.argtypes = [i64] * 7
         lib.ora_codelet_cost.restype = i64
-        lib.ora_inspect.argtypes = [ctypes.c_int, i32, P, P, i32, ctypes.c_int, P, P, P, P, P,
+        lib.ora_inspect.argtypes = [ctypes.c_int, i32, P, P, i32, ctypes.c_int, P, i32, P, P, P, P,
                                     ctypes.POINTER(ctypes.POINTER(i64)), ctypes.POINTER(i64)]
         lib.ora_check_plan.argtypes = [ctypes.c_int, i32, P, P, P, P, i32, P, P, i64,
                                        ctypes.POINTER(i64)]
@@ -130,6 +132,31 @@ def level_order(lev: np.ndarray, depth: int):
     return lp, perm[:n]
 
 
+def coarse_order(lev: np.ndarray, depth: int, rows_per_block: int):
+    """(part_ptr, perm): rows sorted by (row // R, level, row); one partition per
+    non-empty (block, level) pair (LBC-style coarsening, Sec. IV-A)."""
+    n = lev.size
+    lev = np.ascontiguousarray(lev, dtype=np.int32)
+    pp = np.empty(n + 1, dtype=np.int32)
+    perm = np.empty(max(n, 1), dtype=np.int32)
+    npart = ctypes.c_int32(0)
+    rc = _L().ora_coarse_order(n, _p(lev), depth, int(rows_per_block), _p(pp), _p(perm), ctypes.byref(npart))
+    if rc:
+        raise OracleError(ERR.get(rc, str(rc)))
+    return pp[:npart.value + 1].copy(), perm[:n].copy()
+
+
+def check_schedule(lo, perm, part_ptr):
+    """(code, row): code 0 when every dependency of every row lies in a strictly
+    earlier partition; 1 (with the row) when one does not; 2 when malformed."""
+    n, rp, ci = _csr(lo)
+    perm = np.ascontiguousarray(perm, dtype=np.int32)
+    pp = np.ascontiguousarray(part_ptr, dtype=np.int32)
+    bad = ctypes.c_int32(-1)
+    rc = _L().ora_check_schedule(n, _p(rp), _p(ci), _p(perm), _p(pp), pp.size - 1, ctypes.byref(bad))
+    return int(rc), int(bad.value)
+
+
 def codelet_cost(p, s_f, s_g, s_h, weights=PAPER_WEIGHTS) -> int:
     """Eq. 1: c = w_op |p| + w_cl + w_idx (|s_f| + |s_g| + |s_h|)."""
     return int(_L().ora_codelet_cost(p, s_f, s_g, s_h, *weights))
@@ -149,8 +176,11 @@ class Plan:
 
 
 def inspect(a, kind: int, t: int = 256, allowed: int = ALLOW_ALL,
-            weights=(8, 32, 4)) -> Plan:
-    """Algorithm 1 on the pattern of ``a`` for kind SPMV or SPTRSV."""
+            weights=(8, 32, 4), coarsen: int = 0) -> Plan:
+    """Algorithm 1 on the pattern of ``a`` for kind SPMV or SPTRSV.
+
+    ``coarsen`` = R > 0 partitions a SpTRSV by (block of R rows, level)
+    instead of by level (LBC-style coarsening, Sec. IV-A)."""
     n, rp, ci = _csr(a)
     perm = np.empty(max(n, 1), dtype=np.int32)
     lp = np.empty(n + 2, dtype=np.int32)
@@ -159,7 +189,7 @@ def inspect(a, kind: int, t: int = 256, allowed: int = ALLOW_ALL,
     w = np.asarray(weights, dtype=np.int64)
     out = ctypes.POINTER(ctypes.c_int64)()
     ncod = ctypes.c_int64(0)
-    rc = _L().ora_inspect(kind, n, _p(rp), _p(ci), int(t), int(allowed), _p(w), _p(perm), _p(lp),
+    rc = _L().ora_inspect(kind, n, _p(rp), _p(ci), int(t), int(allowed), _p(w), int(coarsen), _p(perm), _p(lp),
                           ctypes.byref(nparts), _p(gs), ctypes.byref(out), ctypes.byref(ncod))
     if rc:
         raise OracleError(ERR.get(rc, str(rc)))

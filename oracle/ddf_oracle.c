@@ -11,6 +11,8 @@
  *   ora_sptrsv_csr      forward substitution L x = b     (Sec. V baseline)
  *   ora_levels          longest-path levels of G         (Sec. IV-A, findDependencies)
  *   ora_level_order     rows ordered by (level, row)     (Sec. IV-A, partitionIterationSpace)
+ *   ora_coarse_order    coarsened partitions: (block of R rows, level)  (Sec. IV-A, LBC; R14)
+ *   ora_check_schedule  every dependency in an earlier partition (Sec. IV-A)
  *   ora_inspect         Algorithm 1 (DDF inspector)      (Sec. IV-A, Alg. 1, Sec. III-C/D)
  *   ora_check_plan      plan expansion == CSR trace       (Sec. III-A definitions)
  *   ora_codelet_cost    Eq. 1 with weights               (Sec. III-C, Eq. 1)
@@ -38,6 +40,10 @@
  *       and g addresses a copy of the off-diagonal values laid out in that
  *       level order.
  *   R6  Regions are windows of t consecutive positions of a partition.
+ *   R14 Coarsened partitions (the paper partitions SpTRSV with LBC, Sec. IV-A):
+ *       rows are cut into blocks of R consecutive rows; the partitions are the
+ *       non-empty (block, level) pairs in increasing block then level order,
+ *       rows increasing inside one.  R = 0 gives the plain level sets (R5).
  *   R7  Strategies: BLAS_first takes maximal BLAS runs from every row whose
  *       own columns are evenly spaced, then maximal PSC I runs of >= 2 rows in
  *       the gaps, then PSC II runs of what is left; PSCI_first takes maximal
@@ -130,6 +136,59 @@ int ora_level_order(int32_t n, const int32_t* lev, int32_t depth, int32_t* level
     for (int32_t i = 0; i < n; ++i) perm[fill[lev[i]]++] = i;
     free(fill);
     return ORA_OK;
+}
+
+/* Coarsened order (R14): rows sorted by (row / R, level, row); a partition
+ * starts wherever the block or the level changes.  part_ptr needs n + 1
+ * entries; the number of partitions is stored in *nparts. */
+int ora_coarse_order(int32_t n, const int32_t* lev, int32_t depth, int32_t R, int32_t* part_ptr,
+                     int32_t* perm, int32_t* nparts) {
+    if (R < 1) return ORA_ERR_ARG;
+    int32_t* cnt = (int32_t*)malloc(sizeof(int32_t) * (size_t)(depth + 1));
+    if (!cnt) return ORA_ERR_OOM;
+    int32_t np = 0, q = 0;
+    for (int64_t b0 = 0; b0 < n; b0 += R) {             /* each block, in order */
+        int32_t b1 = (int32_t)(b0 + R < n ? b0 + R : n);
+        for (int32_t l = 0; l <= depth; ++l) cnt[l] = 0;
+        for (int32_t i = (int32_t)b0; i < b1; ++i) cnt[lev[i] + 1]++;
+        for (int32_t l = 0; l < depth; ++l) cnt[l + 1] += cnt[l];
+        for (int32_t l = 0; l < depth; ++l)              /* non-empty levels of the block */
+            if (cnt[l + 1] > cnt[l]) part_ptr[np++] = q + cnt[l];
+        for (int32_t i = (int32_t)b0; i < b1; ++i) perm[q + cnt[lev[i]]++] = i;
+        q = b1;
+    }
+    part_ptr[np] = n;
+    *nparts = np;
+    free(cnt);
+    return ORA_OK;
+}
+
+/* Schedule check: every off-diagonal dependency j of row i (L_ij != 0, j < i)
+ * sits in a partition strictly before the partition of i.  Returns 0, or 1
+ * with the offending row in *bad, or 2 when perm / part_ptr are malformed. */
+int ora_check_schedule(int32_t n, const int32_t* Lp, const int32_t* Li, const int32_t* perm,
+                       const int32_t* part_ptr, int32_t nparts, int32_t* bad) {
+    *bad = -1;
+    int32_t* part = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    if (!part) return 99;
+    for (int32_t i = 0; i < n; ++i) part[i] = -1;
+    int rc = 0;
+    if (nparts < 0 || part_ptr[0] != 0 || part_ptr[nparts] != n) rc = 2;
+    for (int32_t p = 0; p < nparts && !rc; ++p) {
+        if (part_ptr[p + 1] <= part_ptr[p]) { rc = 2; break; }
+        for (int32_t q = part_ptr[p]; q < part_ptr[p + 1]; ++q) {
+            int32_t r = perm[q];
+            if (r < 0 || r >= n || part[r] >= 0) { rc = 2; break; }
+            part[r] = p;
+        }
+    }
+    for (int32_t i = 0; i < n && !rc; ++i)
+        for (int32_t k = Lp[i]; k < Lp[i + 1]; ++k) {
+            int32_t j = Li[k];
+            if (j < i && part[j] >= part[i]) { rc = 1; *bad = i; break; }
+        }
+    free(part);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -351,16 +410,17 @@ static void emit(const afun* a, const fopd* d, int64_t part, const piece* c, int
 /*
  * Algorithm 1 for K in {SpMV, SpTRSV} on the CSR pattern (Ap, Ai).
  * Outputs (caller-allocated, sizes n / n+1):
- *   perm[n]          partition sequence (identity for SpMV, level order for SpTRSV)
+ *   perm[n]          partition sequence (identity for SpMV, level order for SpTRSV,
+ *                    (block, level) order for SpTRSV with coarsen = R > 0, R14)
  *   level_ptr[n+1]   partition boundaries; *nparts partitions
  *   gs[n]            start of each position's points in the executor's value array
  * and a malloc'd array of canonical records (*out, *ncod records of NF int64).
  * weights = {w_op, w_cl, w_idx}.
  */
 int ora_inspect(int kind, int32_t n, const int32_t* Ap, const int32_t* Ai, int32_t t,
-                int allowed, const int64_t* weights, int32_t* perm, int32_t* level_ptr,
-                int32_t* nparts, int64_t* gs, int64_t** out, int64_t* ncod) {
-    if (n < 0 || t < 1 || !(allowed & ALLOW_PSC2)) return ORA_ERR_ARG;
+                int allowed, const int64_t* weights, int32_t coarsen, int32_t* perm,
+                int32_t* level_ptr, int32_t* nparts, int64_t* gs, int64_t** out, int64_t* ncod) {
+    if (n < 0 || t < 1 || !(allowed & ALLOW_PSC2) || coarsen < 0) return ORA_ERR_ARG;
     *out = NULL;
     *ncod = 0;
     int32_t* len = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
@@ -390,9 +450,14 @@ int ora_inspect(int kind, int32_t n, const int32_t* Ap, const int32_t* Ai, int32
         }
         int32_t depth = ora_levels(n, Ap, Ai, lev);
         if (depth < 0) { free(lev); free(len); free(cs); return ORA_ERR_NOT_LOWER; }
-        int rc = ora_level_order(n, lev, depth, level_ptr, perm);
+        int rc;
+        if (coarsen > 0) {
+            rc = ora_coarse_order(n, lev, depth, coarsen, level_ptr, perm, nparts);   /* R14 */
+        } else {
+            rc = ora_level_order(n, lev, depth, level_ptr, perm);
+            *nparts = depth;
+        }
         if (rc) { free(lev); free(len); free(cs); return rc; }
-        *nparts = depth;
         int64_t acc = 0;
         for (int32_t q = 0; q < n; ++q) {
             int32_t r = perm[q];

@@ -364,3 +364,110 @@ def test_checker_catches_planted_mistakes():
     # dropping a record leaves positions uncovered
     rc, _ = oracle.check_plan(a, oracle.SPMV, p.perm, p.level_ptr, p.gs, np.delete(p.records, i, 0))
     assert rc == 9
+
+
+# ---------------------------------------------------------------------------
+# Coarsened SpTRSV partitions (LBC-style, Sec. IV-A): (block of R rows, level)
+# ---------------------------------------------------------------------------
+
+def brute_levels(lo):
+    """Longest incoming path of every row by repeated relaxation (no ordering)."""
+    n = lo.n_rows
+    lev = np.zeros(n, np.int64)
+    changed = True
+    while changed:
+        changed = False
+        for i in range(n):
+            for k in range(lo.rowptr[i], lo.rowptr[i + 1]):
+                j = lo.colidx[k]
+                if j < i and lev[j] + 1 > lev[i]:
+                    lev[i] = lev[j] + 1
+                    changed = True
+    return lev
+
+
+COARSE_MATS = {
+    "lap5_9": lambda: synth.lower_triangle(synth.laplacian_5pt(9)),
+    "lap7_5": lambda: synth.lower_triangle(synth.laplacian_7pt(5)),
+    "elast_3": lambda: synth.lower_triangle(synth.elasticity_blocks(3)),
+    "powerlaw_300": lambda: synth.lower_triangle(synth.powerlaw(300), "unit_dominant"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(COARSE_MATS))
+@pytest.mark.parametrize("R", [1, 7, 32, 100])
+def test_coarse_order_is_sorted_by_block_level_row(name, R):
+    lo = COARSE_MATS[name]()
+    lev = brute_levels(lo)
+    depth = int(lev.max()) + 1
+    pp, perm = oracle.coarse_order(lev.astype(np.int32), depth, R)
+    keys = [(i // R, int(lev[i]), i) for i in range(lo.n_rows)]
+    want = sorted(range(lo.n_rows), key=lambda i: keys[i])
+    assert perm.tolist() == want
+    starts = [q for q in range(lo.n_rows) if q == 0 or keys[want[q]][:2] != keys[want[q - 1]][:2]]
+    assert pp.tolist() == starts + [lo.n_rows]
+    assert oracle.check_schedule(lo, perm, pp) == (0, -1)
+
+
+@pytest.mark.parametrize("name", sorted(COARSE_MATS))
+def test_one_block_equals_level_sets(name):
+    lo = COARSE_MATS[name]()
+    plain = oracle.inspect(lo, oracle.SPTRSV)
+    for R in (lo.n_rows, lo.n_rows + 5, 1 << 20):
+        c = oracle.inspect(lo, oracle.SPTRSV, coarsen=R)
+        assert np.array_equal(c.perm, plain.perm)
+        assert np.array_equal(c.level_ptr, plain.level_ptr)
+        assert np.array_equal(c.records, plain.records)
+
+
+@pytest.mark.parametrize("name", sorted(COARSE_MATS))
+@pytest.mark.parametrize("R", [16, 50])
+def test_coarse_plans_expand_to_the_trace(name, R):
+    lo = COARSE_MATS[name]()
+    c = oracle.inspect(lo, oracle.SPTRSV, coarsen=R)
+    assert oracle.check_plan(lo, oracle.SPTRSV, c.perm, c.level_ptr, c.gs, c.records) == (0, -1)
+    assert oracle.check_schedule(lo, c.perm, c.level_ptr) == (0, -1)
+    # every partition holds rows of one block and one level
+    lev, _ = oracle.levels(lo)
+    for p in range(c.nparts):
+        rows = c.perm[c.level_ptr[p]:c.level_ptr[p + 1]]
+        assert len({int(r) // R for r in rows}) == 1
+        assert len({int(lev[r]) for r in rows}) == 1
+        assert np.all(np.diff(rows) > 0)
+
+
+@pytest.mark.parametrize("k", [4, 6, 9])
+def test_lap7_plane_blocks_partition_count(k):
+    # 7-point lower triangle on a k^3 grid, level(x, y, z) = x + y + z.  With
+    # one z-plane per block (R = k^2) the plane holds levels z .. z + 2k - 2:
+    # 2k - 1 partitions per block, k (2k - 1) in total.
+    lo = synth.lower_triangle(synth.laplacian_7pt(k))
+    c = oracle.inspect(lo, oracle.SPTRSV, coarsen=k * k)
+    assert c.nparts == k * (2 * k - 1)
+    plain = oracle.inspect(lo, oracle.SPTRSV)
+    assert plain.nparts == 3 * k - 2
+
+
+def test_schedule_check_catches_planted_mistakes():
+    lo = COARSE_MATS["lap7_5"]()
+    plain = oracle.inspect(lo, oracle.SPTRSV)
+    perm, pp = plain.perm.copy(), plain.level_ptr.copy()
+    assert oracle.check_schedule(lo, perm, pp) == (0, -1)
+    # a row moved into the partition before its own level
+    q = int(pp[3])
+    r = int(perm[q])
+    bad = perm.copy()
+    bad[q], bad[q - 1] = bad[q - 1], bad[q]
+    code, row = oracle.check_schedule(lo, bad, pp)
+    assert code == 1
+    # two partitions merged into one (a row then shares a partition with a dependency)
+    merged = np.delete(pp, 2)
+    assert oracle.check_schedule(lo, perm, merged)[0] == 1
+    # rows sorted by (row, level): not a schedule
+    assert oracle.check_schedule(lo, np.arange(lo.n_rows, dtype=np.int32),
+                                 np.array([0, lo.n_rows], np.int32))[0] == 1
+    # a row listed twice is malformed
+    dup = perm.copy()
+    dup[1] = dup[0]
+    assert oracle.check_schedule(lo, dup, pp)[0] == 2
+    assert r >= 0
