@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--coarsen", type=int, default=None,
+                    help="SpTRSV rows per block (coarsen_rows; 0 = plain level sets; default: library default)")
     return ap.parse_args()
 
 
@@ -148,6 +150,8 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     phases = ("inspect_spmv", "spmv", "inspect_sptrsv", "sptrsv")
 
+    opts_L = ddf.ddf_opts_default(coarsen_rows=args.coarsen) if args.coarsen is not None else None
+
     def step(record):
         evs = []
         stats = []
@@ -158,7 +162,7 @@ def run_ours(args, rank, world, local_rank):
             e[1].record(stream)
             ddf.ddf_spmv(pA, d["x"], d["y"])
             e[2].record(stream)
-            pL = ddf.ddf_inspect(*d["L"], d["lo"].n_cols, ddf.DDF_SPTRSV)
+            pL = ddf.ddf_inspect(*d["L"], d["lo"].n_cols, ddf.DDF_SPTRSV, opts_L)
             e[3].record(stream)
             ddf.ddf_sptrsv(pL, d["b"], d["xs"])
             e[4].record(stream)
@@ -225,7 +229,9 @@ def run_ours(args, rank, world, local_rank):
             "sptrsv_ms": round(t_trsv, 4),
             "sptrsv_gbs": round(sl["bytes_exec"] / (t_trsv * 1e-3) / 1e9, 1),
             "sptrsv_bytes": sl["bytes_exec"],
-            "depth": sl["depth"],
+            "depth": sl["levels"],
+            "partitions": sl["depth"],
+            "blocks": sl["blocks"],
             "codelets_spmv": sa["ncodelets"], "ops_spmv": sa["ops"],
             "codelets_sptrsv": sl["ncodelets"], "ops_sptrsv": sl["ops"],
         }

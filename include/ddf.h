@@ -104,8 +104,17 @@ typedef struct {
     int32_t unit_nnz;       /* executor work unit: target nonzeros per warp (default 256)     */
     int32_t store_dtype;    /* DDF_F64 (default), or DDF_F32 / DDF_BF16 for the mixed-precision
                                executors (the plan then also keeps a low-precision copy)     */
-    int32_t reserved[8];
+    int32_t coarsen_rows;   /* SpTRSV partitions (Sec. IV-A, LBC-style coarsening):
+                               0 = level sets of G; R in 1..DDF_COARSEN_MAX_ROWS = the
+                               non-empty (block of R consecutive rows, level) pairs, in block
+                               then level order.  A coarsened plan is solved one block per
+                               CTA, dependencies inside a block through shared memory
+                               (default DDF_COARSEN_DEFAULT_ROWS = 0: level sets)             */
+    int32_t reserved[7];
 } ddf_opts;
+
+#define DDF_COARSEN_MAX_ROWS 16384
+#define DDF_COARSEN_DEFAULT_ROWS 0
 
 /* Plan statistics (counts per codelet type are indexed by ddf_codelet_type). */
 typedef struct {
@@ -118,7 +127,9 @@ typedef struct {
     int64_t nunits;                       /* executor work units                              */
     int64_t bytes_exec;                   /* algorithmic bytes of one execute call            */
     int64_t max_row_len;
-    int64_t reserved[6];
+    int64_t levels;                       /* SpTRSV: depth of G (longest path + 1)          */
+    int64_t blocks;                       /* SpTRSV: row blocks of a coarsened plan, else 0   */
+    int64_t reserved[4];
 } ddf_plan_stats_t;
 
 /* Fill *o with the defaults listed above.  Never fails for a non-NULL o. */

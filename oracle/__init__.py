@@ -31,6 +31,9 @@ ALLOW_BLAS, ALLOW_PSC1, ALLOW_PSC2 = 1, 2, 4
 ALLOW_ALL = 7
 #: Eq. 1 exactly as printed: |p| + m + sum |s_d| with m = 3 access functions
 PAPER_WEIGHTS = (1, 3, 1)
+#: rows per block of coarsened SpTRSV partitions; the CUDA library's default
+#: option value, so that default plans on both sides are comparable
+DEFAULT_COARSEN = 0
 #: record layout of one codelet (12 x int64)
 FIELDS = ("part", "type", "q0", "m", "n", "f_str", "rho", "g_str", "gamma", "h0", "delta", "sigma")
 
@@ -176,11 +179,11 @@ class Plan:
 
 
 def inspect(a, kind: int, t: int = 256, allowed: int = ALLOW_ALL,
-            weights=(8, 32, 4), coarsen: int = 0) -> Plan:
+            weights=(8, 32, 4), coarsen: int = DEFAULT_COARSEN) -> Plan:
     """Algorithm 1 on the pattern of ``a`` for kind SPMV or SPTRSV.
 
     ``coarsen`` = R > 0 partitions a SpTRSV by (block of R rows, level)
-    instead of by level (LBC-style coarsening, Sec. IV-A)."""
+    (LBC-style coarsening, Sec. IV-A); 0 gives the plain level sets."""
     n, rp, ci = _csr(a)
     perm = np.empty(max(n, 1), dtype=np.int32)
     lp = np.empty(n + 2, dtype=np.int32)

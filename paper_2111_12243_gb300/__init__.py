@@ -38,6 +38,8 @@ EXPORTS = ("ddf_opts_default", "ddf_inspect", "ddf_update_values", "ddf_spmv", "
            "ddf_inspect_batch", "ddf_spmm", "ddf_sptrsm", "ddf_tune", "ddf_plan_save", "ddf_plan_load")
 #: rows accepted by ddf_sptrsv_csr_noalloc (the size of its static scratch)
 DDF_NOALLOC_MAX_ROWS = 1 << 20
+DDF_COARSEN_MAX_ROWS = 16384
+DDF_COARSEN_DEFAULT_ROWS = 0
 
 
 class DDFLibraryMissing(ImportError):
@@ -60,7 +62,8 @@ class ddf_opts(ctypes.Structure):
     _fields_ = [("window_t", ctypes.c_int32), ("allowed_types", ctypes.c_int32),
                 ("w_op", ctypes.c_int64), ("w_codelet", ctypes.c_int64), ("w_index", ctypes.c_int64),
                 ("spin_cap_ns", ctypes.c_int64), ("unit_nnz", ctypes.c_int32),
-                ("store_dtype", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
+                ("store_dtype", ctypes.c_int32), ("coarsen_rows", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
 
 
 class ddf_plan_stats_t(ctypes.Structure):
@@ -69,7 +72,7 @@ class ddf_plan_stats_t(ctypes.Structure):
                 ("ncodelets", ctypes.c_int64 * 3), ("ops", ctypes.c_int64 * 3),
                 ("rows", ctypes.c_int64 * 3), ("nunits", ctypes.c_int64),
                 ("bytes_exec", ctypes.c_int64), ("max_row_len", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 6)]
+                ("levels", ctypes.c_int64), ("blocks", ctypes.c_int64), ("reserved", ctypes.c_int64 * 4)]
 
 
 _lib = None
@@ -356,7 +359,7 @@ def ddf_plan_stats(plan: Plan) -> dict:
     return {"kind": s.kind, "n_rows": s.n_rows, "n_cols": s.n_cols, "depth": s.depth, "nnz": s.nnz,
             "points": s.points, "ncodelets": list(s.ncodelets), "ops": list(s.ops),
             "rows": list(s.rows), "nunits": s.nunits, "bytes_exec": s.bytes_exec,
-            "max_row_len": s.max_row_len}
+            "max_row_len": s.max_row_len, "levels": s.levels, "blocks": s.blocks}
 
 
 def ddf_plan_export(plan: Plan) -> dict:

@@ -48,6 +48,12 @@ void release(ddf_plan_s* p) {
     ddf_free(p->rlp, s);
     ddf_free(p->xlp, s);
     ddf_free(p->nrm, s);
+    ddf_free(p->blk_ptr, s);
+    ddf_free(p->esplit, s);
+    ddf_free(p->qcod, s);
+    ddf_free(p->chunk_q0, s);
+    ddf_free(p->chunk_meta, s);
+    ddf_free(p->blk_chunk, s);
 }
 
 ddf_status check_opts(const ddf_opts* o) {
@@ -56,6 +62,7 @@ ddf_status check_opts(const ddf_opts* o) {
     if (o->w_op < 0 || o->w_codelet < 0 || o->w_index < 0) return DDF_ERR_ARG;
     if (o->spin_cap_ns <= 0 || o->unit_nnz < 1) return DDF_ERR_ARG;
     if (o->store_dtype != DDF_F64 && o->store_dtype != DDF_F32 && o->store_dtype != DDF_BF16) return DDF_ERR_ARG;
+    if (o->coarsen_rows < 0 || o->coarsen_rows > DDF_COARSEN_MAX_ROWS) return DDF_ERR_ARG;
     return DDF_OK;
 }
 
@@ -179,6 +186,7 @@ void ddf_opts_default(ddf_opts* o) {
     o->w_index = 4;
     o->spin_cap_ns = 2000000000ll;
     o->unit_nnz = 256;
+    o->coarsen_rows = DDF_COARSEN_DEFAULT_ROWS;
 }
 
 const char* ddf_status_string(ddf_status st) {

@@ -252,6 +252,150 @@ __global__ void k_part_ptr(int32_t n, const uint32_t* __restrict__ ls, int32_t* 
 }
 
 // ---------------------------------------------------------------------------
+// Coarsened partitions (LBC-style, Sec. IV-A): rows in blocks of R consecutive
+// rows; inside a block, one partition per level.  The level order is sorted a
+// second time, stably, by block, which gives (block, level, row).
+// ---------------------------------------------------------------------------
+__global__ void k_block_key(int32_t n, const int32_t* __restrict__ seq, int32_t R, uint32_t* __restrict__ key) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) key[q] = (uint32_t)(seq[q] / R);
+}
+
+// flag[q] = 1 where a partition starts: the block or the level changes.
+__global__ void k_coarse_flags(int32_t n, const int32_t* __restrict__ seq, const uint32_t* __restrict__ key,
+                               const int32_t* __restrict__ lev, int32_t* __restrict__ flag) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    flag[q] = (q == 0 || key[q] != key[q - 1] || lev[seq[q]] != lev[seq[q - 1]]) ? 1 : 0;
+}
+
+// part_ptr / blk_ptr from the exclusive scan `off` of the flags; pid[q] is the
+// partition of position q (the mining step's partition key).
+__global__ void k_coarse_fill(int32_t n, const uint32_t* __restrict__ key, const int32_t* __restrict__ flag,
+                              const int64_t* __restrict__ off, int32_t npart, int32_t nblocks,
+                              int32_t* __restrict__ pp, int32_t* __restrict__ bp, uint32_t* __restrict__ pid) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int32_t id = (int32_t)(off[q + 1] - 1);
+    pid[q] = (uint32_t)id;
+    if (flag[q]) {
+        pp[id] = (int32_t)q;
+        if (q == 0 || key[q] != key[q - 1]) bp[key[q]] = id;
+    }
+    if (q == 0) {
+        pp[npart] = n;
+        bp[nblocks] = npart;
+    }
+}
+
+// esplit[q]: how many of position q's off-diagonal columns lie before the first
+// row of its block (they are read from other blocks; the rest from this one).
+// Columns are increasing inside a row.
+__global__ void k_esplit(int32_t n, const int32_t* __restrict__ seq, const int32_t* __restrict__ st,
+                         const int32_t* __restrict__ col, int32_t R, int32_t* __restrict__ es) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int32_t base = (seq[q] / R) * R;
+    int32_t lo = st[q], hi = st[q + 1];
+    const int32_t a = lo;
+    while (lo < hi) {
+        const int32_t mid = lo + ((hi - lo) >> 1);
+        if (col[mid] < base) lo = mid + 1;
+        else hi = mid;
+    }
+    es[q] = lo - a;
+}
+
+// qcod[q] = codelet covering position q.
+__global__ void k_qcod(int64_t ncod, const dcod* __restrict__ cod, int32_t* __restrict__ qc) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncod) return;
+    const int32_t q0 = cod[c].q0, m = cod[c].m;
+    for (int32_t i = 0; i < m; ++i) qc[q0 + i] = (int32_t)c;
+}
+
+__device__ __forceinline__ int32_t pow2_at_least(int32_t need) {
+    int32_t v = 1;
+    while (v < need && v < 32) v <<= 1;
+    return v;
+}
+
+__device__ __forceinline__ int32_t pow2_at_most(int32_t lim) {
+    int32_t v = 1;
+    while (v * 2 <= lim && v < 32) v <<= 1;
+    return v;
+}
+
+// Chunks of the coarsened solve: each partition is cut greedily, in position
+// order, into runs of at most DDF_BLK_ROWS_CAP rows and DDF_BLK_ENT_CAP points;
+// a row with more points than that is a chunk of its own ("direct").  One
+// thread per partition; write == false only counts.
+template <bool write>
+__device__ int32_t chunk_partition(int32_t a, int32_t b, const int32_t* __restrict__ st,
+                                   const int32_t* __restrict__ es, const int32_t* __restrict__ qc,
+                                   const dcod* __restrict__ cod, int32_t* __restrict__ cq0,
+                                   int32_t* __restrict__ cmeta) {
+    int32_t k = 0;
+    int32_t q = a;
+    while (q < b) {
+        const int32_t c0 = q;
+        int32_t rows = 0, ents = 0, mi = 0, ml = 0, flags = 0;
+        const int32_t L0 = st[q + 1] - st[q];
+        if (L0 > DDF_BLK_ENT_CAP) {
+            rows = 1;
+            mi = L0 - es[q];
+            ml = L0;
+            flags = DDF_CK_DIRECT;
+            ++q;
+        } else {
+            while (q < b && rows < DDF_BLK_ROWS_CAP) {
+                const int32_t L = st[q + 1] - st[q];
+                if (L > DDF_BLK_ENT_CAP || ents + L > DDF_BLK_ENT_CAP) break;
+                ents += L;
+                ++rows;
+                mi = max(mi, L - es[q]);
+                ml = max(ml, L);
+                if (write && cod[qc[q]].type == DDF_PSC2) flags |= DDF_CK_PSC2;
+                ++q;
+            }
+        }
+        if (write) {
+            const int32_t vch = min(pow2_at_most(DDF_BLK_CHAIN_LANES / rows),
+                                    pow2_at_least((mi + DDF_BLK_CHAIN_PER_LANE - 1) / DDF_BLK_CHAIN_PER_LANE));
+            const int32_t vpr = pow2_at_least((ml + DDF_BLK_PROD_PER_LANE - 1) / DDF_BLK_PROD_PER_LANE);
+            cq0[k] = c0;
+            cmeta[k] = vch | (vpr << 8) | flags;
+        }
+        ++k;
+    }
+    return k;
+}
+
+__global__ void k_chunk_count(int32_t npart, const int32_t* __restrict__ pp, const int32_t* __restrict__ st,
+                              const int32_t* __restrict__ es, int32_t* __restrict__ cnt) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= npart) return;
+    cnt[g] = chunk_partition<false>(pp[g], pp[g + 1], st, es, nullptr, nullptr, nullptr, nullptr);
+}
+
+__global__ void k_chunk_fill(int32_t npart, const int32_t* __restrict__ pp, const int32_t* __restrict__ st,
+                             const int32_t* __restrict__ es, const int32_t* __restrict__ qc,
+                             const dcod* __restrict__ cod, const int64_t* __restrict__ coff, int32_t n,
+                             int32_t* __restrict__ cq0, int32_t* __restrict__ cmeta) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= npart) return;
+    const int64_t o = coff[g];
+    chunk_partition<true>(pp[g], pp[g + 1], st, es, qc, cod, cq0 + o, cmeta + o);
+    if (g == 0) cq0[coff[npart]] = n;
+}
+
+__global__ void k_blk_chunk(int32_t nblocks, const int32_t* __restrict__ bp, const int64_t* __restrict__ coff,
+                            int32_t* __restrict__ bc) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b <= nblocks) bc[b] = (int32_t)coff[bp[b]];
+}
+
+// ---------------------------------------------------------------------------
 // SpTRSV relayout: off-diagonal columns and values of the rows in level order
 // ---------------------------------------------------------------------------
 __global__ void k_rel_lens(int32_t n, const int32_t* __restrict__ perm, const int32_t* __restrict__ rp,
@@ -862,6 +1006,8 @@ void fill_stats(ddf_plan_s* p, const std::vector<dcod>& hc) {
     S.n_rows = p->n;
     S.n_cols = p->n_cols;
     S.depth = p->depth;
+    S.levels = p->kind == DDF_SPTRSV ? p->nlevels : 0;
+    S.blocks = p->nblocks;
     S.nnz = p->nnz;
     S.points = p->npts;
     int64_t psc2_nof = 0, s_entries = 0;
@@ -933,6 +1079,7 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
         TRY(d2h(&hstat, p->status, 1, s));
         if (hstat) return (ddf_status)hstat;
         p->depth = n > 0 ? hmax + 1 : 0;   // hmax is the largest level
+        p->nlevels = p->depth;
         // partitionIterationSpace: rows sorted by (level, row)
         TRY(ddf_alloc(&p->seq, n, s));
         TRY(tmp.get(&lsorted, n));
@@ -940,12 +1087,38 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
         k_iota_u32<<<ddf_grid(n, TPB, 4096), TPB, 0, s>>>(p->seq, n);
         ddf_count_launch();
         TRY(ddf_radix_sort_u32(lsorted, p->seq, n, (uint32_t)(p->depth > 0 ? p->depth - 1 : 0), s));
-        TRY(ddf_alloc(&p->part_ptr, (int64_t)p->depth + 1, s));
-        if (n > 0) {
-            k_part_ptr<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, lsorted, p->part_ptr, p->depth);
+        const int32_t R = p->opts.coarsen_rows;
+        if (R > 0 && n > 0) {
+            // coarsened: stable second sort by block, partitions = (block, level)
+            p->nblocks = (int32_t)(((int64_t)n + R - 1) / R);
+            uint32_t* key = nullptr;
+            int32_t* flag = nullptr;
+            int64_t* foff = nullptr;
+            TRY(tmp.get(&key, n));
+            TRY(tmp.get(&flag, n));
+            TRY(tmp.get(&foff, (int64_t)n + 1));
+            k_block_key<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, p->seq, R, key);
             ddf_count_launch();
+            TRY(ddf_radix_sort_u32(key, p->seq, n, (uint32_t)(p->nblocks - 1), s));
+            k_coarse_flags<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, p->seq, key, lev, flag);
+            ddf_count_launch();
+            TRY(ddf_scan_i32_to_i64(flag, foff, n, s));
+            int64_t npart = 0;
+            TRY(d2h(&npart, foff + n, 1, s));
+            p->depth = (int32_t)npart;
+            TRY(ddf_alloc(&p->part_ptr, npart + 1, s));
+            TRY(ddf_alloc(&p->blk_ptr, (int64_t)p->nblocks + 1, s));
+            k_coarse_fill<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, key, flag, foff, p->depth, p->nblocks, p->part_ptr,
+                                                         p->blk_ptr, lsorted);
+            ddf_count_launch();
+        } else {
+            TRY(ddf_alloc(&p->part_ptr, (int64_t)p->depth + 1, s));
+            if (n > 0) {
+                k_part_ptr<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, lsorted, p->part_ptr, p->depth);
+                ddf_count_launch();
+            }
+            else DDF_CUDA_TRY(cudaMemsetAsync(p->part_ptr, 0, sizeof(int32_t), s));
         }
-        else DDF_CUDA_TRY(cudaMemsetAsync(p->part_ptr, 0, sizeof(int32_t), s));
         // level-ordered copy of the off-diagonal entries
         int32_t* lens = nullptr;
         int64_t* st64 = nullptr;
@@ -962,8 +1135,10 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
         TRY(ddf_alloc(&p->starts, (int64_t)n + 1, s));
         k_i64_to_i32<<<ddf_grid(n + 1, TPB, 4096), TPB, 0, s>>>(st64, p->starts, (int64_t)n + 1);
         ddf_count_launch();
-        TRY(ddf_alloc(&p->col, npts, s));
-        TRY(ddf_alloc(&p->val, npts, s));
+        // DDF_TAIL_PAD spare elements: the coarsened solve stages ranges of
+        // these arrays with 16-byte-granular bulk copies
+        TRY(ddf_alloc(&p->col, npts + DDF_TAIL_PAD, s));
+        TRY(ddf_alloc(&p->val, npts + DDF_TAIL_PAD, s));
         TRY(ddf_alloc(&p->dinv, n, s));
         if (p->opts.store_dtype != DDF_F64) TRY(ddf_alloc(&p->diag, n, s));
         if (n > 0) {
@@ -972,6 +1147,11 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
             ddf_count_launch();
         }
         DDF_CUDA_TRY(cudaGetLastError());
+        if (p->nblocks > 0) {
+            TRY(ddf_alloc(&p->esplit, n, s));
+            k_esplit<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, p->seq, p->starts, p->col, R, p->esplit);
+            ddf_count_launch();
+        }
         // keep the inspected rowptr for ddf_update_values
         p->orig_rowptr = const_cast<int32_t*>(rowptr);
     }
@@ -1044,6 +1224,35 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
         ddf_count_launch();
     }
     DDF_CUDA_TRY(cudaGetLastError());
+    if (p->nblocks > 0) {
+        TRY(ddf_alloc(&p->qcod, n, s));
+        if (ncod > 0) {
+            k_qcod<<<ddf_grid(ncod, TPB), TPB, 0, s>>>(ncod, p->cod, p->qcod);
+            ddf_count_launch();
+        }
+        // chunks of the coarsened solve
+        const int32_t np = p->depth;
+        int32_t* ccnt = nullptr;
+        int64_t* coff = nullptr;
+        TRY(tmp.get(&ccnt, np));
+        TRY(tmp.get(&coff, (int64_t)np + 1));
+        k_chunk_count<<<ddf_grid(np, 128), 128, 0, s>>>(np, p->part_ptr, p->starts, p->esplit, ccnt);
+        ddf_count_launch();
+        TRY(ddf_scan_i32_to_i64(ccnt, coff, np, s));
+        int64_t nck = 0;
+        TRY(d2h(&nck, coff + np, 1, s));
+        p->nchunks = nck;
+        TRY(ddf_alloc(&p->chunk_q0, nck + 1, s));
+        TRY(ddf_alloc(&p->chunk_meta, nck, s));
+        TRY(ddf_alloc(&p->blk_chunk, (int64_t)p->nblocks + 1, s));
+        k_chunk_fill<<<ddf_grid(np, 128), 128, 0, s>>>(np, p->part_ptr, p->starts, p->esplit, p->qcod, p->cod,
+                                                       coff, n, p->chunk_q0, p->chunk_meta);
+        ddf_count_launch();
+        k_blk_chunk<<<ddf_grid((int64_t)p->nblocks + 1, TPB), TPB, 0, s>>>(p->nblocks, p->blk_ptr, coff,
+                                                                          p->blk_chunk);
+        ddf_count_launch();
+        DDF_CUDA_TRY(cudaGetLastError());
+    }
 
     // executor units
     TRY(ddf_build_units(p, s));

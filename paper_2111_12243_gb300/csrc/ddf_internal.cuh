@@ -11,6 +11,21 @@
 #define DDF_MAX_T 512          // largest mining window t (local mask of 512 bits)
 #define DDF_WARPS_PER_CTA 8
 #define DDF_CTA_THREADS (32 * DDF_WARPS_PER_CTA)
+// Coarsened solve: a partition is cut into chunks of at most DDF_BLK_ROWS_CAP
+// rows and DDF_BLK_ENT_CAP points, the unit staged into shared memory; a row
+// longer than DDF_BLK_ENT_CAP is a chunk of its own, run from global memory.
+#define DDF_BLK_ROWS_CAP 64
+#define DDF_TAIL_PAD 8            // spare elements after val / col / val_lp
+#define DDF_BLK_ENT_CAP 768
+#define DDF_BLK_CHAIN_LANES 256   // threads of the chain role
+#define DDF_BLK_PROD_PER_LANE 8   // points per producer lane per batch
+#define DDF_BLK_CHAIN_PER_LANE 1  // in-block points per chain lane (more lanes per row shorten
+                                  // the dependent chain, which sets the chunk's latency)
+// chunk_meta bits
+#define DDF_CK_VCHAIN(m) ((m) & 0xff)
+#define DDF_CK_VPROD(m) (((m) >> 8) & 0xff)
+#define DDF_CK_PSC2 (1 << 16)
+#define DDF_CK_DIRECT (1 << 17)
 
 // Executor codelet descriptor (64 bytes).  Access functions of the codelet's
 // rows i0 in [0, m) and points i1 in [0, n):
@@ -78,6 +93,18 @@ struct ddf_plan_s {
     float* rlp;                   // residual rounded to FP32 (right-hand side of a correction)
     float* xlp;                   // low-precision solution / correction
     double* nrm;                  // two FP64 accumulators (||b||^2, ||r||^2)
+    // coarsened SpTRSV plans (opts.coarsen_rows = R > 0): partitions are the
+    // (block of R rows, level) pairs; part_ptr then has depth + 1 entries with
+    // depth = number of partitions, and nlevels is the depth of G
+    int32_t nlevels;              // SpTRSV: depth of G
+    int32_t nblocks;              // coarsened: ceil(n / R); 0 otherwise
+    int32_t* blk_ptr;             // [nblocks + 1] first partition of each block
+    int32_t* esplit;              // [n] entries of position q with a column before its block
+    int32_t* qcod;                // [n] codelet holding position q
+    int64_t nchunks;              // coarsened: chunks of all partitions
+    int32_t* chunk_q0;            // [nchunks + 1] first position of each chunk
+    int32_t* chunk_meta;          // [nchunks] lanes per row and flags (DDF_CK_*)
+    int32_t* blk_chunk;           // [nblocks + 1] first chunk of each block
     // statistics, computed on the first ddf_plan_stats call
     int32_t stats_ready;
     ddf_plan_stats_t stats;

@@ -92,8 +92,8 @@ ddf_status ddf_make_lowp(ddf_plan_s* p, cudaStream_t s) {
     const int64_t nv = p->kind == DDF_SPMV ? p->nnz : p->npts;
     p->vdtype = dt;
     if (!p->val_lp && nv > 0) {
-        ddf_status st = dt == DDF_F32 ? ddf_alloc((float**)&p->val_lp, nv, s)
-                                      : ddf_alloc((__nv_bfloat16**)&p->val_lp, nv, s);
+        ddf_status st = dt == DDF_F32 ? ddf_alloc((float**)&p->val_lp, nv + DDF_TAIL_PAD, s)
+                                      : ddf_alloc((__nv_bfloat16**)&p->val_lp, nv + DDF_TAIL_PAD, s);
         if (st) return st;
     }
     if (p->kind == DDF_SPTRSV && p->n > 0) {

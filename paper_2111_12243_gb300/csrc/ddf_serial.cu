@@ -17,12 +17,13 @@
 namespace {
 
 constexpr char MAGIC[8] = {'D', 'D', 'F', 'P', 'L', 'A', 'N', '1'};
-constexpr int32_t VERSION = 1;
+constexpr int32_t VERSION = 2;
 
 struct Header {
     char magic[8];
     int32_t version, kind, n, n_cols, depth, has_values, vdtype, units_per_cta;
-    int64_t nnz, npts, ncod, ncod_type[3], nunits[3];
+    int32_t nlevels, nblocks;
+    int64_t nnz, npts, ncod, ncod_type[3], nunits[3], nchunks;
     ddf_opts opts;
 };
 
@@ -46,7 +47,7 @@ size_t value_size(int32_t dt) { return dt == DDF_F32 ? 4 : (dt == DDF_BF16 ? 2 :
 
 // The arrays of a plan in file order (pointers of p; sizes from the header).
 // slots[k] receives the address of the plan field that holds piece k.
-std::vector<Piece> pieces(ddf_plan_s* p, const Header& h, void** slots[16]) {
+std::vector<Piece> pieces(ddf_plan_s* p, const Header& h, void** slots[24]) {
     const int64_t n = h.n, nv = h.kind == DDF_SPMV ? h.nnz : h.npts;
     const bool tr = h.kind == DDF_SPTRSV;
     const bool lp = h.vdtype != DDF_F64;
@@ -66,6 +67,14 @@ std::vector<Piece> pieces(ddf_plan_s* p, const Header& h, void** slots[16]) {
         add((void**)&p->seq, 4 * (size_t)n);
         add((void**)&p->dinv, 8 * (size_t)n);
         add((void**)&p->orig_rowptr, 4 * (size_t)(n + 1));
+        if (h.nblocks > 0) {
+            add((void**)&p->blk_ptr, 4 * (size_t)(h.nblocks + 1));
+            add((void**)&p->esplit, 4 * (size_t)n);
+            add((void**)&p->qcod, 4 * (size_t)n);
+            add((void**)&p->chunk_q0, 4 * (size_t)(h.nchunks + 1));
+            add((void**)&p->chunk_meta, 4 * (size_t)h.nchunks);
+            add((void**)&p->blk_chunk, 4 * (size_t)(h.nblocks + 1));
+        }
     }
     if (lp) {
         add((void**)&p->val_lp, value_size(h.vdtype) * (size_t)nv);
@@ -89,6 +98,9 @@ Header header_of(ddf_plan_s* p) {
     h.has_values = p->has_values;
     h.vdtype = p->vdtype;
     h.units_per_cta = p->units_per_cta;
+    h.nlevels = p->nlevels;
+    h.nblocks = p->nblocks;
+    h.nchunks = p->nchunks;
     h.nnz = p->nnz;
     h.npts = p->npts;
     h.ncod = p->ncod;
@@ -113,7 +125,7 @@ extern "C" {
 ddf_status ddf_plan_save(ddf_plan_t p, void* buf, size_t* len) {
     if (!p || !len) return DDF_ERR_ARG;
     Header h = header_of(p);
-    void** slots[16];
+    void** slots[24];
     std::vector<Piece> v = pieces(p, h, slots);
     const size_t need = total_bytes(v);
     if (!buf) {
@@ -154,7 +166,9 @@ ddf_status ddf_plan_load(const void* buf, size_t len, ddf_stream_t stream, ddf_p
     // every counted element takes at least one byte of the buffer: this bounds
     // the sizes below (no overflow) before they are summed
     const int64_t cap = (int64_t)len;
-    if (h.n >= cap || h.depth >= cap || h.nnz > cap || h.npts > cap || h.ncod > cap || h.nunits[0] > cap ||
+    if (h.nblocks < 0 || h.nlevels < 0 || h.nchunks < 0 || h.nchunks > (int64_t)len || (h.nblocks > 0 && (h.kind != DDF_SPTRSV || h.opts.coarsen_rows < 1)))
+        return DDF_ERR_ARG;
+    if (h.n >= cap || h.depth >= cap || h.nblocks >= cap || h.nnz > cap || h.npts > cap || h.ncod > cap || h.nunits[0] > cap ||
         h.nunits[1] > cap || h.nunits[2] > cap)
         return DDF_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -167,6 +181,9 @@ ddf_status ddf_plan_load(const void* buf, size_t len, ddf_stream_t stream, ddf_p
     p->has_values = h.has_values;
     p->vdtype = h.vdtype;
     p->units_per_cta = h.units_per_cta;
+    p->nlevels = h.nlevels;
+    p->nblocks = h.nblocks;
+    p->nchunks = h.nchunks;
     for (int t = 0; t < 3; ++t) {
         if (h.ncod_type[t] < 0) st = DDF_ERR_ARG;
         p->ncod_type[t] = h.ncod_type[t];
@@ -176,7 +193,7 @@ ddf_status ddf_plan_load(const void* buf, size_t len, ddf_stream_t stream, ddf_p
         ddf_plan_destroy(p);
         return st;
     }
-    void** slots[16];
+    void** slots[24];
     std::vector<Piece> v = pieces(p, h, slots);
     const unsigned char* in = (const unsigned char*)buf;
     const size_t need = total_bytes(v);
@@ -197,7 +214,8 @@ ddf_status ddf_plan_load(const void* buf, size_t len, ddf_stream_t stream, ddf_p
         const size_t b = v[i].bytes;
         if (b > 0) {
             void* d = nullptr;
-            if (cudaMallocAsync(&d, b, s) != cudaSuccess) {
+            // 16 spare bytes: val / col / val_lp are staged by 16-byte-granular bulk copies
+            if (cudaMallocAsync(&d, b + 16, s) != cudaSuccess) {
                 (void)cudaGetLastError();
                 st = DDF_ERR_OOM;
                 break;

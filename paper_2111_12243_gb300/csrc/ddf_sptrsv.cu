@@ -21,6 +21,8 @@
 // for ddf_sptrsv, and FP32 vectors with FP32 or BF16 values for the
 // low-precision solves of ddf_sptrsv_refine (the flag pattern is then the
 // 32-bit NaN 0xFFFFFFFF).
+#include <algorithm>
+
 #include "ddf_internal.cuh"
 
 namespace {
@@ -208,6 +210,388 @@ k_sptrsv(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64_t 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Coarsened solve (plans with coarsen_rows = R > 0).  The partitions of a
+// block of R consecutive rows are that block's level sets, so one CTA runs a
+// whole block: the block's x lives in shared memory (xs), a dependency inside
+// the block costs a shared-memory read behind a CTA-local barrier instead of
+// a flag hop through L2, and only columns before the block's first row (the
+// "external" prefix of a row, esplit[q] points) are read from other blocks
+// through the x-as-flag protocol of the plain solve.
+//
+// The inspector cut every partition into chunks (at most DDF_BLK_ROWS_CAP rows
+// and DDF_BLK_ENT_CAP points, positions consecutive), so a chunk's values and
+// columns are one contiguous range of the plan's arrays.  Warp roles:
+//   producers (BLK_PROD warps, one staging slot each): chunk k of the block
+//     goes to producer k mod BLK_PROD.  It stages the chunk's values (and, for
+//     chunks with PSC II rows, columns) into its slot with bulk copies (TMA,
+//     completion on an mbarrier), reads each row's codelet, sets
+//     xs[r - base] = b[r] - (external sum), rewrites each in-block column as
+//     an offset into xs, and publishes the chunk.
+//   chain (BLK_CHAIN warps): chunks in order; each row subtracts its in-block
+//     points (all operands in shared memory), scales by 1 / L_ii, stores x in
+//     xs and in global x; a named barrier among the chain warps ends a chunk.
+// A producer reuses its slot only after the chain has finished the slot's
+// previous chunk.  Blocks come from a ticket in increasing order and a block
+// reads only rows of earlier blocks, which hold a ticket and run, so every
+// wait ends; each is bounded by spin_cap_ns like those of the plain solve.
+// ---------------------------------------------------------------------------
+constexpr int BLK_CHAIN = DDF_BLK_CHAIN_LANES / 32;
+constexpr int BLK_PROD_MAX = 12;                // producer warps (= staging slots), at most
+constexpr int BLK_PB = DDF_BLK_PROD_PER_LANE;   // external points per producer lane per batch
+
+__host__ __device__ constexpr int round16(int b) { return (b + 15) & ~15; }
+
+// Byte layout of one staging slot: the chunk's values and columns (bulk
+// copies, up to 15 bytes of alignment slack at each end), then per row its
+// xs offset, value start, length, external count, and 1 / L_ii.
+template <typename TV, typename TX>
+struct SlotLayout {
+    static constexpr int VAL = round16(DDF_BLK_ENT_CAP * (int)sizeof(TV) + 32);
+    static constexpr int COL = round16(DDF_BLK_ENT_CAP * 4 + 32);
+    static constexpr int META = DDF_BLK_ROWS_CAP * 16;            // int4 per row
+    static constexpr int DINV = round16(DDF_BLK_ROWS_CAP * (int)sizeof(TX));
+    static constexpr int BYTES = VAL + COL + META + DINV;
+};
+
+struct BlkShared {
+    unsigned long long bar[BLK_PROD_MAX];   // one mbarrier per slot
+    int32_t blk;
+    int32_t chain_done;                     // chunks of the block finished by the chain
+    int32_t ext_done[BLK_PROD_MAX];         // chunks finished by each producer
+    int32_t crows[BLK_PROD_MAX];            // rows of the slot's current chunk
+    int32_t cmeta[BLK_PROD_MAX];            // chunk_meta of the slot's current chunk
+    int32_t dv[BLK_PROD_MAX], dc[BLK_PROD_MAX];   // element shift of the staged ranges
+    int32_t e0[BLK_PROD_MAX];               // first value index of the chunk
+    double red[BLK_CHAIN];                  // direct rows: per-warp partial sums
+};
+
+__device__ __forceinline__ int32_t ld_vol(const int32_t* p) { return *(const volatile int32_t*)p; }
+__device__ __forceinline__ void st_vol(int32_t* p, int32_t v) { *(volatile int32_t*)p = v; }
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Bounded wait for a slot's staging to land.  The copies read this GPU's own
+// memory and always complete; should the cap still run out the status is
+// latched and the wait goes on for one more cap, so that no copy is left in
+// flight when the kernel ends.
+__device__ __noinline__ void mbar_wait(unsigned long long* bar, uint32_t parity, int32_t* status,
+                                       uint32_t* abort_flag, int64_t cap_ns) {
+    uint64_t t0 = ddf_globaltimer();
+    bool late = false;
+    while (!mbar_try_wait(bar, parity)) {
+        if ((int64_t)(ddf_globaltimer() - t0) > cap_ns) {
+            if (late) return;
+            late = true;
+            ddf_set_status(status, DDF_ERR_TIMEOUT);
+            atomicExch(abort_flag, 1u);
+            t0 = ddf_globaltimer();
+        }
+    }
+}
+
+// Bounded wait until a shared counter reaches `need`.
+__device__ __noinline__ void wait_count(const int32_t* c, int32_t need, int32_t* status, uint32_t* abort_flag,
+                                        int64_t cap_ns) {
+    uint64_t t0 = ddf_globaltimer();
+    uint32_t it = 0;
+    while (ld_vol(c) < need) {
+        if (++it > 8) __nanosleep(32);
+        if ((it & 63u) == 0) {
+            if (ddf_ld_relaxed_s32((const int32_t*)abort_flag) != 0) return;
+            if ((int64_t)(ddf_globaltimer() - t0) > cap_ns) {
+                ddf_set_status(status, DDF_ERR_TIMEOUT);
+                atomicExch(abort_flag, 1u);
+                return;
+            }
+        }
+    }
+}
+
+// 16-byte-granular range [a, z) of an array: aligned start, byte count, and
+// the element shift of a inside the copied range.
+struct Range16 {
+    const unsigned char* src;
+    uint32_t bytes;
+    int32_t shift;
+};
+template <typename T>
+__device__ __forceinline__ Range16 range16(const T* a, const T* z) {
+    const uintptr_t pa = (uintptr_t)a, pz = (uintptr_t)z;
+    const uintptr_t a16 = pa & ~(uintptr_t)15, z16 = (pz + 15) & ~(uintptr_t)15;
+    return Range16{(const unsigned char*)a16, (uint32_t)(z16 - a16), (int32_t)((pa - a16) / sizeof(T))};
+}
+
+template <typename TV, typename TX>
+__global__ void __launch_bounds__(DDF_BLK_CHAIN_LANES + 32 * BLK_PROD_MAX, 1)
+k_sptrsv_blk(const int32_t* __restrict__ chunk_q0, const int32_t* __restrict__ chunk_meta,
+             const int32_t* __restrict__ blk_chunk, const int32_t* __restrict__ esplit, int32_t nblocks, int32_t R,
+             const int32_t* __restrict__ seq, const int32_t* __restrict__ st, const int32_t* __restrict__ col,
+             const TV* __restrict__ val, const TX* __restrict__ dinv, const TX* __restrict__ b, TX* x,
+             uint32_t* ticket, int32_t* status, int64_t cap_ns) {
+    using B = XBits<TX>;
+    using SL = SlotLayout<TV, TX>;
+    extern __shared__ __align__(16) unsigned char blk_dsm[];
+    TX* xs = reinterpret_cast<TX*>(blk_dsm);
+    unsigned char* slots = blk_dsm + round16(R * (int)sizeof(TX));
+    __shared__ BlkShared S;
+    uint32_t* abort_flag = ticket + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nprod = (int)(blockDim.x >> 5) - BLK_CHAIN;
+    if (threadIdx.x < nprod) mbar_init(&S.bar[threadIdx.x]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    uint32_t phase = 0;   // parity of this producer's slot barrier (kept across blocks)
+    while (true) {
+        if (threadIdx.x == 0) {
+            S.blk = (int32_t)atomicAdd(ticket, 1u);
+            S.chain_done = 0;
+        }
+        if (threadIdx.x < nprod) S.ext_done[threadIdx.x] = 0;
+        __syncthreads();
+        const int32_t blk = S.blk;
+        if (blk >= nblocks) break;
+        const int32_t base = blk * R;
+        const int32_t c0 = blk_chunk[blk], nck = blk_chunk[blk + 1] - c0;
+        if (warp >= BLK_CHAIN) {
+            // ------------------------------ producer ------------------------------
+            const int e = warp - BLK_CHAIN;
+            unsigned char* slot = slots + (size_t)e * SL::BYTES;
+            TV* svals = reinterpret_cast<TV*>(slot);
+            int32_t* scols = reinterpret_cast<int32_t*>(slot + SL::VAL);
+            int4* smeta = reinterpret_cast<int4*>(slot + SL::VAL + SL::COL);
+            TX* sdinv = reinterpret_cast<TX*>(slot + SL::VAL + SL::COL + SL::META);
+            for (int32_t k = e; k < nck; k += nprod) {
+                if (k >= nprod) {
+                    if (lane == 0) wait_count(&S.chain_done, k - nprod + 1, status, abort_flag, cap_ns);
+                    __syncwarp();
+                }
+                const int32_t qa = chunk_q0[c0 + k], qb = chunk_q0[c0 + k + 1];
+                const int32_t meta = chunk_meta[c0 + k];
+                const bool direct = (meta & DDF_CK_DIRECT) != 0;
+                const int32_t e0 = st[qa], e1 = st[qb];
+                // stage the chunk's values and columns (one contiguous range each)
+                Range16 rv{nullptr, 0, 0}, rc{nullptr, 0, 0};
+                if (!direct && e1 > e0) {
+                    rv = range16(val + e0, val + e1);
+                    rc = range16(col + e0, col + e1);
+                }
+                if (lane == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_expect_tx(&S.bar[e], rv.bytes + rc.bytes);
+                    if (rv.bytes) bulk_g2s(svals, rv.src, rv.bytes, &S.bar[e]);
+                    if (rc.bytes) bulk_g2s(scols, rc.src, rc.bytes, &S.bar[e]);
+                }
+                // one lane per row while the copies fly: row (the plan's row map),
+                // value extent, external count, 1 / L_ii; xs[r - base] = b[r]
+                const int32_t rows = qb - qa;
+                for (int32_t i = lane; i < rows; i += 32) {
+                    const int32_t q = qa + i;
+                    const int32_t r = seq[q], kb = st[q], L = st[q + 1] - kb, ns = esplit[q];
+                    smeta[i] = make_int4(r - base, kb - e0, L, ns);
+                    sdinv[i] = dinv[q];
+                    xs[r - base] = b[r];
+                }
+                mbar_wait(&S.bar[e], phase, status, abort_flag, cap_ns);
+                phase ^= 1u;
+                __syncwarp();
+                // v lanes per row: external sums; in-block columns become xs offsets
+                const int v = DDF_CK_VPROD(meta);
+                const int lg = __ffs(v) - 1, rpw = 32 >> lg, sub = lane >> lg, li = lane & (v - 1);
+                for (int32_t ib = 0; ib < rows; ib += rpw) {
+                    const int32_t i = ib + sub;
+                    const bool act = i < rows;
+                    TX acc = 0;
+                    int32_t roff = 0;
+                    if (act) {
+                        const int4 m = smeta[i];
+                        roff = m.x;
+                        const int32_t kbl = m.y, L = m.z, ns = m.w;
+                        for (int32_t i1b = 0; i1b < ns; i1b += BLK_PB * v) {
+                            typename B::U xv[BLK_PB];
+                            TX vv[BLK_PB];
+                            int32_t jj[BLK_PB];
+#pragma unroll
+                            for (int t = 0; t < BLK_PB; ++t) {
+                                const int32_t i1 = i1b + li + t * v;
+                                jj[t] = -1;
+                                vv[t] = 0;
+                                if (i1 < ns) {
+                                    jj[t] = direct ? col[e0 + kbl + i1] : scols[rc.shift + kbl + i1];
+                                    vv[t] = ddf_cvt<TX>(direct ? val[e0 + kbl + i1] : svals[rv.shift + kbl + i1]);
+                                }
+                            }
+#pragma unroll
+                            for (int t = 0; t < BLK_PB; ++t)
+                                xv[t] = jj[t] >= 0 ? B::ld(x + jj[t]) : (typename B::U)0;
+#pragma unroll
+                            for (int t = 0; t < BLK_PB; ++t) {
+                                if (jj[t] < 0) continue;
+                                if (xv[t] == B::SENT) {
+                                    TX w = wait_x<TX>(x + jj[t], status, abort_flag, cap_ns);
+                                    xv[t] = B::bits(w) == B::SENT ? B::CANON : B::bits(w);
+                                }
+                                acc += vv[t] * B::val(xv[t]);
+                            }
+                        }
+                        if (!direct)
+                            for (int32_t i1 = ns + li; i1 < L; i1 += v) scols[rc.shift + kbl + i1] -= base;
+                    }
+                    for (int o = v >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    if (act && li == 0) xs[roff] -= acc;
+                }
+                if (lane == 0) {
+                    S.crows[e] = rows;
+                    S.cmeta[e] = meta;
+                    S.dv[e] = rv.shift;
+                    S.dc[e] = rc.shift;
+                    S.e0[e] = e0;
+                }
+                __syncwarp();
+                __threadfence_block();
+                if (lane == 0) st_vol(&S.ext_done[e], k / nprod + 1);
+            }
+        } else {
+            // ------------------------------- chain --------------------------------
+            const int ct = threadIdx.x;   // 0 .. DDF_BLK_CHAIN_LANES - 1
+            for (int32_t k = 0; k < nck; ++k) {
+                const int e = k % nprod;
+                if (lane == 0) wait_count(&S.ext_done[e], k / nprod + 1, status, abort_flag, cap_ns);
+                __syncwarp();
+                __threadfence_block();
+                const unsigned char* slot = slots + (size_t)e * SL::BYTES;
+                const TV* svals = reinterpret_cast<const TV*>(slot);
+                const int32_t* scols = reinterpret_cast<const int32_t*>(slot + SL::VAL);
+                const int4* smeta = reinterpret_cast<const int4*>(slot + SL::VAL + SL::COL);
+                const TX* sdinv = reinterpret_cast<const TX*>(slot + SL::VAL + SL::COL + SL::META);
+                const int32_t rows = S.crows[e], meta = S.cmeta[e], dv = S.dv[e], dc = S.dc[e];
+                if (!(meta & DDF_CK_DIRECT)) {
+                    const int v = DDF_CK_VCHAIN(meta);
+                    const int lg = __ffs(v) - 1, li = ct & (v - 1);
+                    const int32_t slot_i = ct >> lg, stride = DDF_BLK_CHAIN_LANES >> lg, wslot = (warp * 32) >> lg;
+                    for (int32_t ib = 0; ib + wslot < rows; ib += stride) {
+                        const int32_t i = ib + slot_i;
+                        const bool act = i < rows;
+                        TX acc = 0, acc2 = 0;
+                        int32_t roff = 0;
+                        if (act) {
+                            const int4 m = smeta[i];
+                            roff = m.x;
+                            const TV* pv = svals + dv + m.y;
+                            const int32_t* pc = scols + dc + m.y;
+                            // offsets of a valid plan lie in [0, R); anything else is
+                            // read through the flag protocol (bounded).  Two sums in
+                            // flight halve the dependent FMA chain.
+                            auto xat = [&](int32_t o) -> TX {
+                                return (uint32_t)o < (uint32_t)R ? xs[o] : dep<TX>(x, base + o, status, abort_flag, cap_ns);
+                            };
+                            int32_t i1 = m.w + li;
+                            for (; i1 + v < m.z; i1 += 2 * v) {
+                                acc += ddf_cvt<TX>(pv[i1]) * xat(pc[i1]);
+                                acc2 += ddf_cvt<TX>(pv[i1 + v]) * xat(pc[i1 + v]);
+                            }
+                            if (i1 < m.z) acc += ddf_cvt<TX>(pv[i1]) * xat(pc[i1]);
+                            acc += acc2;
+                        }
+                        for (int o = v >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                        if (act && li == 0) {
+                            TX xr = (xs[roff] - acc) * sdinv[i];
+                            typename B::U bits = B::bits(xr);
+                            if (bits == B::SENT) bits = B::CANON;
+                            xs[roff] = B::val(bits);
+                            B::st(x + base + roff, bits);
+                        }
+                    }
+                } else {
+                    // one row longer than a slot: in-block points from global memory
+                    const int4 m = smeta[0];
+                    const int32_t kb = S.e0[e] + m.y;
+                    TX acc = 0;
+                    for (int32_t i1 = m.w + ct; i1 < m.z; i1 += DDF_BLK_CHAIN_LANES) {
+                        const int32_t j = col[kb + i1];
+                        const TX xj = (uint32_t)(j - base) < (uint32_t)R ? xs[j - base]
+                                                                         : dep<TX>(x, j, status, abort_flag, cap_ns);
+                        acc += ddf_cvt<TX>(val[kb + i1]) * xj;
+                    }
+                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    if (lane == 0) S.red[warp] = (double)acc;
+                    asm volatile("bar.sync 1, %0;" ::"n"(DDF_BLK_CHAIN_LANES) : "memory");
+                    if (ct == 0) {
+                        TX tot = 0;
+                        for (int w = 0; w < BLK_CHAIN; ++w) tot += (TX)S.red[w];
+                        TX xr = (xs[m.x] - tot) * sdinv[0];
+                        typename B::U bits = B::bits(xr);
+                        if (bits == B::SENT) bits = B::CANON;
+                        xs[m.x] = B::val(bits);
+                        B::st(x + base + m.x, bits);
+                    }
+                }
+                asm volatile("bar.sync 1, %0;" ::"n"(DDF_BLK_CHAIN_LANES) : "memory");
+                if (ct == 0) st_vol(&S.chain_done, k + 1);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Shared memory of the coarsened solve for R rows per block and `nprod` slots.
+template <typename TV, typename TX>
+size_t blocked_smem(int32_t R, int nprod) {
+    return (size_t)round16(R * (int)sizeof(TX)) + (size_t)nprod * SlotLayout<TV, TX>::BYTES;
+}
+
+template <typename TV, typename TX>
+ddf_status launch_blocked(ddf_plan_s* p, const TV* val, const TX* dinv, const TX* b, TX* x, cudaStream_t s) {
+    const int32_t R = p->opts.coarsen_rows;
+    auto kern = k_sptrsv_blk<TV, TX>;
+    int optin = 0;
+    DDF_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+    cudaFuncAttributes fa;
+    DDF_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+    const size_t room = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    // as many producer warps (staging slots) as the shared memory left after xs holds
+    int nprod = BLK_PROD_MAX;
+    while (nprod > 1 && blocked_smem<TV, TX>(R, nprod) > room) --nprod;
+    const size_t smem = blocked_smem<TV, TX>(R, nprod);
+    if (smem > room) return DDF_ERR_ARG;
+    const int threads = DDF_BLK_CHAIN_LANES + 32 * nprod;
+    DDF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    DDF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    if (per_sm < 1) return DDF_ERR_CUDA;
+    const int sm = p->sm_count > 0 ? p->sm_count : 152;
+    int64_t ctas = std::min<int64_t>((int64_t)p->nblocks, (int64_t)per_sm * sm);
+    kern<<<(unsigned)ctas, threads, smem, s>>>(p->chunk_q0, p->chunk_meta, p->blk_chunk, p->esplit, p->nblocks, R,
+                                               p->seq, p->starts, p->col, val, dinv, b, x, p->ticket, p->status,
+                                               p->opts.spin_cap_ns);
+    ddf_count_launch();
+    DDF_CUDA_TRY(cudaGetLastError());
+    return DDF_OK;
+}
+
 template <typename TV, typename TX>
 ddf_status launch_solve(ddf_plan_s* p, const TV* val, const TX* dinv, const TX* b, TX* x, cudaStream_t s) {
     using B = XBits<TX>;
@@ -218,7 +602,11 @@ ddf_status launch_solve(ddf_plan_s* p, const TV* val, const TX* dinv, const TX* 
     ddf_count_launch();
     int launches = 1;
     int64_t nu = p->nunits[0];
-    if (nu > 0) {
+    if (p->nblocks > 0 && p->n > 0) {
+        ddf_status st = launch_blocked<TV, TX>(p, val, dinv, b, x, s);
+        if (st) return st;
+        ++launches;
+    } else if (nu > 0) {
         int per_sm = 0;
         DDF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sptrsv<TV, TX>, DDF_CTA_THREADS, 0));
         if (per_sm < 1) per_sm = 1;

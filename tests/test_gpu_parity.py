@@ -235,23 +235,29 @@ def test_wrong_kind_and_overlap():
     assert e.value.status == 1
 
 
-def test_dependency_wait_times_out_and_recovers():
+@pytest.mark.parametrize("coarsen", [0, 256])
+def test_dependency_wait_times_out_and_recovers(coarsen):
     # Point one off-diagonal entry of a PSC II row r (executed through its
     # column indices) at a row d that itself reads r: r waits for d and d for
     # r, so the wait must run out, latch DDF_ERR_TIMEOUT, and leave the
-    # context usable.
+    # context usable.  In a coarsened plan only entries that name a column
+    # before the row's block go through the flag protocol (the rest are
+    # ordered by the block's own schedule), so the planted entry is the first
+    # entry of a row whose first column lies in an earlier block.
     lo = synth.random_pattern(3000, 3000, 0.003, 17, diag=True, lower=True)
-    q = inspect(lo, 2, spin_cap_ns=50_000_000)
+    q = inspect(lo, 2, spin_cap_ns=50_000_000, coarsen_rows=coarsen)
     exp = ddf.ddf_plan_export(q)
     rec, seq, gs = exp["records"], exp["seq"], exp["gs"]
     offl = np.diff(lo.rowptr) - 1
+    rows_of = np.repeat(np.arange(lo.n_rows), np.diff(lo.rowptr))
     target = None
     for r in rec[(rec[:, 1] == 2) & (rec[:, 0] >= 1)]:
         for pos in range(r[2], r[2] + r[3]):
             row = int(seq[pos])
             if offl[row] < 1:
                 continue
-            rows_of = np.repeat(np.arange(lo.n_rows), np.diff(lo.rowptr))
+            if coarsen and lo.colidx[lo.rowptr[row]] >= (row // coarsen) * coarsen:
+                continue
             deps = rows_of[(lo.colidx == row) & (rows_of != row)]
             if deps.size:
                 target = (int(gs[pos]), int(deps[0]))

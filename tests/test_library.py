@@ -45,11 +45,21 @@ def test_library_loads_and_host_calls(libpath):
     for name in ddf.EXPORTS:
         assert hasattr(L, name)
     o = ddf.ddf_opts_default()
-    assert (o.window_t, o.allowed_types, o.w_op, o.w_codelet, o.w_index, o.unit_nnz) == (
-        256, 7, 8, 32, 4, 256)
+    assert (o.window_t, o.allowed_types, o.w_op, o.w_codelet, o.w_index, o.unit_nnz, o.coarsen_rows) == (
+        256, 7, 8, 32, 4, 256, ddf.DDF_COARSEN_DEFAULT_ROWS)
+    import oracle
+    assert oracle.DEFAULT_COARSEN == ddf.DDF_COARSEN_DEFAULT_ROWS
     assert ddf.ddf_status_string(0) == "ok"
     assert "timed out" in ddf.ddf_status_string(11)
     assert ddf.ddf_status_string(999) == "unknown status"
+
+
+def test_header_constants_match_binding():
+    import re
+    text = open(HEADER).read()
+    for name in ("DDF_COARSEN_MAX_ROWS", "DDF_COARSEN_DEFAULT_ROWS"):
+        m = re.search(r"#define %s (\d+)" % name, text)
+        assert m and int(m.group(1)) == getattr(ddf, name)
 
 
 def test_ctypes_layouts_match_header():
@@ -73,6 +83,9 @@ def test_host_argument_errors_without_gpu(libpath):
     assert L.ddf_inspect(ctypes.byref(A), 1, ctypes.byref(o), None, ctypes.byref(h)) == 1
     o = ddf.ddf_opts_default(allowed_types=ddf.DDF_ALLOW_BLAS)
     assert L.ddf_inspect(ctypes.byref(A), 1, ctypes.byref(o), None, ctypes.byref(h)) == 1
+    for bad in (-1, ddf.DDF_COARSEN_MAX_ROWS + 1):
+        o = ddf.ddf_opts_default(coarsen_rows=bad)
+        assert L.ddf_inspect(ctypes.byref(A), 1, ctypes.byref(o), None, ctypes.byref(h)) == 1
     assert L.ddf_spmv(None, None, None, None) == 1
     assert L.ddf_sptrsv(None, None, None, None) == 1
     assert L.ddf_last_launches(None) == 0
