@@ -83,8 +83,8 @@ __global__ void k_i64_to_i32(const int64_t* __restrict__ in, int32_t* __restrict
 // ---------------------------------------------------------------------------
 // findDependencies: level[i] = 1 + max level of its off-diagonal columns
 // ---------------------------------------------------------------------------
-constexpr int LEV_RPW = 32;                                   // rows per warp, in order
-constexpr int LEV_CHUNK = LEV_RPW * DDF_WARPS_PER_CTA;        // rows per CTA ticket
+constexpr int LEV_CHUNK = 1024;                               // rows per CTA ticket
+constexpr int LEV_MAXSEG = 128;                               // longest run one warp takes at once
 
 // Bounded wait on a level written by another CTA: a few immediate polls, then
 // exponential backoff so that waiting warps do not flood L2 with requests.
@@ -129,16 +129,23 @@ __device__ int32_t wait_level_smem(volatile int32_t* p, int32_t* status, int64_t
     }
 }
 
-// Each CTA takes the next chunk of LEV_CHUNK consecutive rows from a ticket;
-// warp w computes rows [w*LEV_RPW, (w+1)*LEV_RPW) of the chunk in order.
-// Levels of the chunk's rows are also kept in shared memory: a dependency
-// inside the chunk (the common case for banded and stencil matrices) costs a
-// shared-memory read instead of an L2 round trip.  The rows are software
-// pipelined: while row rr is reduced, the column indices of row rr + 1 and
-// the levels of its dependencies outside the chunk are already in flight, so
-// the chain from one row to the next only holds shared-memory work.  Every
-// row waited on has a smaller index, so it belongs to this CTA or to a CTA
-// that already holds a ticket and runs: the waits end.
+// Each CTA takes the next chunk of LEV_CHUNK consecutive rows from a ticket and
+// cuts it into runs: a run starts at every row that does not read the row just
+// before it (the start of a grid line of a stencil, for instance) and at least
+// every LEV_MAXSEG rows.  Warps take runs in increasing order from a counter
+// and compute a run's rows in order, so a chain that follows the rows stays on
+// one warp while the next run, which only waits for the rows it reads, starts
+// on another.  Levels of the chunk's rows are also kept in shared memory: a
+// dependency inside the chunk costs a shared-memory read instead of an L2
+// round trip.  Rows are software pipelined: while row r is reduced, the
+// column indices of row r + 1 and the levels of its dependencies outside the
+// chunk are already in flight.  Every row waited on has a smaller index, so it
+// belongs to a run that a running warp has taken, or to a CTA that already
+// holds a ticket and runs: the waits end.  Large chunks keep many rows in
+// flight per resident thread: with one row per thread too few planes of a
+// 3-D stencil are resident for the wavefront to pipeline.
+constexpr int LEV_WARPS = 16;                                 // warps per CTA
+
 constexpr int LEV_PF = 2;   // dependencies per lane prefetched (rows of up to 64 off-diagonals)
 
 __device__ __forceinline__ void lev_prefetch(int32_t a, int32_t b, int lane, int64_t base,
@@ -154,89 +161,134 @@ __device__ __forceinline__ void lev_prefetch(int32_t a, int32_t b, int lane, int
         l[k] = (j[k] >= 0 && (int64_t)j[k] < base) ? ddf_ld_relaxed_s32(lev + j[k]) : -1;
 }
 
-__global__ void __launch_bounds__(DDF_CTA_THREADS)
+__global__ void __launch_bounds__(32 * LEV_WARPS)
 k_levels(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int32_t* lev,
          uint32_t* ticket, int32_t* maxlev, int32_t* status, int64_t cap_ns) {
-    __shared__ int32_t chunk;
-    __shared__ int32_t wmax[DDF_WARPS_PER_CTA];
+    __shared__ int32_t chunk, nruns, next;
+    __shared__ int32_t wmax[LEV_WARPS];
     __shared__ int32_t slev[LEV_CHUNK];
-    if (threadIdx.x == 0) chunk = (int32_t)atomicAdd(ticket, 1u);
+    __shared__ uint32_t scut[LEV_CHUNK / 32];
+    __shared__ int32_t rstart[LEV_CHUNK + 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        chunk = (int32_t)atomicAdd(ticket, 1u);
+        next = 0;
+    }
     for (int i = threadIdx.x; i < LEV_CHUNK; i += blockDim.x) slev[i] = -1;
     __syncthreads();
-    volatile int32_t* vs = slev;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t base = (int64_t)chunk * LEV_CHUNK;
+    const int32_t rlen = (int32_t)min((int64_t)LEV_CHUNK, (int64_t)n - base);
+    // run starts: rows that do not read the previous row, and every LEV_MAXSEG rows
+    for (int bt = w; bt < LEV_CHUNK / 32; bt += LEV_WARPS) {
+        const int32_t o = bt * 32 + lane;
+        bool cut = false;
+        if (o < rlen) {
+            const int64_t r = base + o;
+            const int32_t e = rp[r + 1] - 1;   // the diagonal is last
+            cut = (o % LEV_MAXSEG) == 0 || !(e > rp[r] && ci[e - 1] == (int32_t)(r - 1));
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, cut);
+        if (lane == 0) scut[bt] = m;
+    }
+    __syncthreads();
+    if (w == 0) {
+        // positions of the set bits, in order (one word per lane)
+        const uint32_t m0 = lane < LEV_CHUNK / 32 ? scut[lane] : 0u;
+        const int c = __popc(m0);
+        int pre = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= o) pre += t;
+        }
+        int k = pre - c;
+        for (uint32_t m = m0; m; m &= m - 1) rstart[k++] = 32 * lane + __ffs(m) - 1;
+        if (lane == 31) {
+            nruns = pre;
+            rstart[pre] = rlen;
+        }
+    }
+    __syncthreads();
+    volatile int32_t* vs = slev;
     int32_t mymax = 0;
-    // row extents of the warp's LEV_RPW rows, one coalesced load per lane
-    const int64_t r0 = base + (int64_t)w * LEV_RPW;
-    int32_t ra_l = 0, rb_l = 0;
-    if (r0 + lane < n) {
-        ra_l = rp[r0 + lane];
-        rb_l = rp[r0 + lane + 1] - 1;   // the diagonal is last: not a dependency
-    }
-    int32_t cj[LEV_PF], cl[LEV_PF];
-    {
-        const int32_t a = __shfl_sync(0xffffffffu, ra_l, 0), b = __shfl_sync(0xffffffffu, rb_l, 0);
-        lev_prefetch(a, r0 < n ? b : a, lane, base, ci, lev, cj, cl);
-    }
-    for (int rr = 0; rr < LEV_RPW; ++rr) {
-        const int64_t r = r0 + rr;
-        if (r >= n) break;
-        const int32_t a = __shfl_sync(0xffffffffu, ra_l, rr), b = __shfl_sync(0xffffffffu, rb_l, rr);
-        // next row's columns and external levels go out now
-        int32_t nj[LEV_PF], nl[LEV_PF];
-        {
-            const bool more = rr + 1 < LEV_RPW && r + 1 < n;
-            const int32_t na = __shfl_sync(0xffffffffu, ra_l, (rr + 1) & 31);
-            const int32_t nb = __shfl_sync(0xffffffffu, rb_l, (rr + 1) & 31);
-            lev_prefetch(na, more ? nb : na, lane, base, ci, lev, nj, nl);
-        }
-        int32_t m = -1;
-#pragma unroll
-        for (int k = 0; k < LEV_PF; ++k) {
-            const int32_t jj = cj[k];
-            if (jj < 0) continue;
-            int32_t lj;
-            if ((int64_t)jj >= base) {
-                lj = vs[jj - base];
-                if (lj < 0) lj = wait_level_smem(vs + (jj - base), status, cap_ns);
-            } else {
-                lj = cl[k];
-                if (lj < 0) lj = wait_level(lev + jj, status, cap_ns);
+    while (true) {
+        int32_t u = 0;
+        if (lane == 0) u = atomicAdd(&next, 1);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= nruns) break;
+        const int32_t ua = rstart[u], ub = rstart[u + 1];
+        for (int32_t sb = ua; sb < ub; sb += 32) {
+            // row extents of the next (up to) 32 rows of the run, one per lane
+            const int64_t r0 = base + sb;
+            const int cnt = min(32, ub - sb);
+            int32_t ra_l = 0, rb_l = 0;
+            if (lane < cnt) {
+                ra_l = rp[r0 + lane];
+                rb_l = rp[r0 + lane + 1] - 1;   // the diagonal is last: not a dependency
             }
-            m = max(m, lj);
-        }
-        for (int32_t k = a + lane + 32 * LEV_PF; k < b; k += 32) {   // rows longer than the prefetch
-            const int32_t jj = ci[k];
-            int32_t lj;
-            if ((int64_t)jj >= base) {
-                lj = vs[jj - base];
-                if (lj < 0) lj = wait_level_smem(vs + (jj - base), status, cap_ns);
-            } else {
-                lj = ddf_ld_relaxed_s32(lev + jj);
-                if (lj < 0) lj = wait_level(lev + jj, status, cap_ns);
+            int32_t cj[LEV_PF], cl[LEV_PF];
+            {
+                const int32_t a = __shfl_sync(0xffffffffu, ra_l, 0), b = __shfl_sync(0xffffffffu, rb_l, 0);
+                lev_prefetch(a, b, lane, base, ci, lev, cj, cl);
             }
-            m = max(m, lj);
-        }
+            for (int rr = 0; rr < cnt; ++rr) {
+                const int64_t r = r0 + rr;
+                const int32_t a = __shfl_sync(0xffffffffu, ra_l, rr), b = __shfl_sync(0xffffffffu, rb_l, rr);
+                // next row's columns and external levels go out now
+                int32_t nj[LEV_PF], nl[LEV_PF];
+                {
+                    const bool more = rr + 1 < cnt;
+                    const int32_t na = __shfl_sync(0xffffffffu, ra_l, (rr + 1) & 31);
+                    const int32_t nb = __shfl_sync(0xffffffffu, rb_l, (rr + 1) & 31);
+                    lev_prefetch(na, more ? nb : na, lane, base, ci, lev, nj, nl);
+                }
+                int32_t m = -1;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) {
-            vs[r - base] = m + 1;
-            ddf_st_relaxed_s32(lev + r, m + 1);
-        }
-        mymax = max(mymax, m + 1);
-        __syncwarp();
+                for (int k = 0; k < LEV_PF; ++k) {
+                    const int32_t jj = cj[k];
+                    if (jj < 0) continue;
+                    int32_t lj;
+                    if ((int64_t)jj >= base) {
+                        lj = vs[jj - base];
+                        if (lj < 0) lj = wait_level_smem(vs + (jj - base), status, cap_ns);
+                    } else {
+                        lj = cl[k];
+                        if (lj < 0) lj = wait_level(lev + jj, status, cap_ns);
+                    }
+                    m = max(m, lj);
+                }
+                for (int32_t k = a + lane + 32 * LEV_PF; k < b; k += 32) {   // rows longer than the prefetch
+                    const int32_t jj = ci[k];
+                    int32_t lj;
+                    if ((int64_t)jj >= base) {
+                        lj = vs[jj - base];
+                        if (lj < 0) lj = wait_level_smem(vs + (jj - base), status, cap_ns);
+                    } else {
+                        lj = ddf_ld_relaxed_s32(lev + jj);
+                        if (lj < 0) lj = wait_level(lev + jj, status, cap_ns);
+                    }
+                    m = max(m, lj);
+                }
 #pragma unroll
-        for (int k = 0; k < LEV_PF; ++k) {
-            cj[k] = nj[k];
-            cl[k] = nl[k];
+                for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if (lane == 0) {
+                    vs[r - base] = m + 1;
+                    ddf_st_relaxed_s32(lev + r, m + 1);
+                }
+                mymax = max(mymax, m + 1);
+                __syncwarp();
+#pragma unroll
+                for (int k = 0; k < LEV_PF; ++k) {
+                    cj[k] = nj[k];
+                    cl[k] = nl[k];
+                }
+            }
         }
     }
     if (lane == 0) wmax[w] = mymax;
     __syncthreads();
     if (threadIdx.x == 0) {
         int32_t t = 0;
-        for (int k = 0; k < DDF_WARPS_PER_CTA; ++k) t = max(t, wmax[k]);
+        for (int k = 0; k < LEV_WARPS; ++k) t = max(t, wmax[k]);
         atomicMax(maxlev, t);
     }
 }
@@ -1069,7 +1121,7 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
         DDF_CUDA_TRY(cudaMemsetAsync(maxlev, 0, sizeof(int32_t), s));
         DDF_CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(int32_t), s));
         if (n > 0) {
-            k_levels<<<ddf_grid(n, LEV_CHUNK), DDF_CTA_THREADS, 0, s>>>(n, rowptr, colidx, lev, tick, maxlev,
+            k_levels<<<ddf_grid(n, LEV_CHUNK), 32 * LEV_WARPS, 0, s>>>(n, rowptr, colidx, lev, tick, maxlev,
                                                                        p->status, p->opts.spin_cap_ns);
             ddf_count_launch();
         }

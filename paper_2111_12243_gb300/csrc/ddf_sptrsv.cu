@@ -299,37 +299,41 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 // memory and always complete; should the cap still run out the status is
 // latched and the wait goes on for one more cap, so that no copy is left in
 // flight when the kernel ends.
-__device__ __noinline__ void mbar_wait(unsigned long long* bar, uint32_t parity, int32_t* status,
+__device__ __noinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity, int32_t* status,
                                        uint32_t* abort_flag, int64_t cap_ns) {
     uint64_t t0 = ddf_globaltimer();
     bool late = false;
     while (!mbar_try_wait(bar, parity)) {
         if ((int64_t)(ddf_globaltimer() - t0) > cap_ns) {
-            if (late) return;
+            if (late) return false;
             late = true;
             ddf_set_status(status, DDF_ERR_TIMEOUT);
             atomicExch(abort_flag, 1u);
             t0 = ddf_globaltimer();
         }
     }
+    return true;
 }
 
-// Bounded wait until a shared counter reaches `need`.
-__device__ __noinline__ void wait_count(const int32_t* c, int32_t need, int32_t* status, uint32_t* abort_flag,
+// Bounded wait until a shared counter reaches `need`.  Returns false when it
+// gave up (this call's abort flag is set, or the cap ran out): the data the
+// counter guards must then not be read.
+__device__ __noinline__ bool wait_count(const int32_t* c, int32_t need, int32_t* status, uint32_t* abort_flag,
                                         int64_t cap_ns) {
     uint64_t t0 = ddf_globaltimer();
     uint32_t it = 0;
     while (ld_vol(c) < need) {
         if (++it > 8) __nanosleep(32);
-        if ((it & 63u) == 0) {
-            if (ddf_ld_relaxed_s32((const int32_t*)abort_flag) != 0) return;
+        if ((it & 63u) == 1) {
+            if (ddf_ld_relaxed_s32((const int32_t*)abort_flag) != 0) return false;
             if ((int64_t)(ddf_globaltimer() - t0) > cap_ns) {
                 ddf_set_status(status, DDF_ERR_TIMEOUT);
                 atomicExch(abort_flag, 1u);
-                return;
+                return false;
             }
         }
     }
+    return true;
 }
 
 // 16-byte-granular range [a, z) of an array: aligned start, byte count, and
@@ -349,8 +353,8 @@ __device__ __forceinline__ Range16 range16(const T* a, const T* z) {
 template <typename TV, typename TX>
 __global__ void __launch_bounds__(DDF_BLK_CHAIN_LANES + 32 * BLK_PROD_MAX, 1)
 k_sptrsv_blk(const int32_t* __restrict__ chunk_q0, const int32_t* __restrict__ chunk_meta,
-             const int32_t* __restrict__ blk_chunk, const int32_t* __restrict__ esplit, int32_t nblocks, int32_t R,
-             const int32_t* __restrict__ seq, const int32_t* __restrict__ st, const int32_t* __restrict__ col,
+             const int32_t* __restrict__ blk_chunk, const int32_t* __restrict__ esplit, int32_t n, int32_t nblocks,
+             int32_t R, const int32_t* __restrict__ seq, const int32_t* __restrict__ st, const int32_t* __restrict__ col,
              const TV* __restrict__ val, const TX* __restrict__ dinv, const TX* __restrict__ b, TX* x,
              uint32_t* ticket, int32_t* status, int64_t cap_ns) {
     using B = XBits<TX>;
@@ -384,10 +388,13 @@ k_sptrsv_blk(const int32_t* __restrict__ chunk_q0, const int32_t* __restrict__ c
             int32_t* scols = reinterpret_cast<int32_t*>(slot + SL::VAL);
             int4* smeta = reinterpret_cast<int4*>(slot + SL::VAL + SL::COL);
             TX* sdinv = reinterpret_cast<TX*>(slot + SL::VAL + SL::COL + SL::META);
+            // a wait that gave up ends this producer's work in the block: it
+            // stages and publishes nothing more, so the chain's waits give up too
             for (int32_t k = e; k < nck; k += nprod) {
                 if (k >= nprod) {
-                    if (lane == 0) wait_count(&S.chain_done, k - nprod + 1, status, abort_flag, cap_ns);
-                    __syncwarp();
+                    int ok = 1;
+                    if (lane == 0) ok = wait_count(&S.chain_done, k - nprod + 1, status, abort_flag, cap_ns);
+                    if (!__shfl_sync(0xffffffffu, ok, 0)) break;
                 }
                 const int32_t qa = chunk_q0[c0 + k], qb = chunk_q0[c0 + k + 1];
                 const int32_t meta = chunk_meta[c0 + k];
@@ -415,9 +422,9 @@ k_sptrsv_blk(const int32_t* __restrict__ chunk_q0, const int32_t* __restrict__ c
                     sdinv[i] = dinv[q];
                     xs[r - base] = b[r];
                 }
-                mbar_wait(&S.bar[e], phase, status, abort_flag, cap_ns);
+                const bool landed = mbar_wait(&S.bar[e], phase, status, abort_flag, cap_ns);
                 phase ^= 1u;
-                __syncwarp();
+                if (!__all_sync(0xffffffffu, landed)) break;
                 // v lanes per row: external sums; in-block columns become xs offsets
                 const int v = DDF_CK_VPROD(meta);
                 const int lg = __ffs(v) - 1, rpw = 32 >> lg, sub = lane >> lg, li = lane & (v - 1);
@@ -442,6 +449,10 @@ k_sptrsv_blk(const int32_t* __restrict__ chunk_q0, const int32_t* __restrict__ c
                                 if (i1 < ns) {
                                     jj[t] = direct ? col[e0 + kbl + i1] : scols[rc.shift + kbl + i1];
                                     vv[t] = ddf_cvt<TX>(direct ? val[e0 + kbl + i1] : svals[rv.shift + kbl + i1]);
+                                    if ((uint32_t)jj[t] >= (uint32_t)n) {   // not a column: no read
+                                        jj[t] = -1;
+                                        acc = B::val(B::CANON);
+                                    }
                                 }
                             }
 #pragma unroll
@@ -479,15 +490,19 @@ k_sptrsv_blk(const int32_t* __restrict__ chunk_q0, const int32_t* __restrict__ c
             const int ct = threadIdx.x;   // 0 .. DDF_BLK_CHAIN_LANES - 1
             for (int32_t k = 0; k < nck; ++k) {
                 const int e = k % nprod;
-                if (lane == 0) wait_count(&S.ext_done[e], k / nprod + 1, status, abort_flag, cap_ns);
-                __syncwarp();
+                int ok = 1;
+                if (lane == 0) ok = wait_count(&S.ext_done[e], k / nprod + 1, status, abort_flag, cap_ns);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
                 __threadfence_block();
                 const unsigned char* slot = slots + (size_t)e * SL::BYTES;
                 const TV* svals = reinterpret_cast<const TV*>(slot);
                 const int32_t* scols = reinterpret_cast<const int32_t*>(slot + SL::VAL);
                 const int4* smeta = reinterpret_cast<const int4*>(slot + SL::VAL + SL::COL);
                 const TX* sdinv = reinterpret_cast<const TX*>(slot + SL::VAL + SL::COL + SL::META);
-                const int32_t rows = S.crows[e], meta = S.cmeta[e], dv = S.dv[e], dc = S.dc[e];
+                // the slot is read only after its producer published it; a warp whose
+                // wait gave up takes the chunk's shape from the plan and skips the work
+                const int32_t meta = ok ? S.cmeta[e] : chunk_meta[c0 + k];
+                const int32_t rows = ok ? S.crows[e] : 0, dv = S.dv[e], dc = S.dc[e];
                 if (!(meta & DDF_CK_DIRECT)) {
                     const int v = DDF_CK_VCHAIN(meta);
                     const int lg = __ffs(v) - 1, li = ct & (v - 1);
@@ -506,7 +521,9 @@ k_sptrsv_blk(const int32_t* __restrict__ chunk_q0, const int32_t* __restrict__ c
                             // read through the flag protocol (bounded).  Two sums in
                             // flight halve the dependent FMA chain.
                             auto xat = [&](int32_t o) -> TX {
-                                return (uint32_t)o < (uint32_t)R ? xs[o] : dep<TX>(x, base + o, status, abort_flag, cap_ns);
+                                if ((uint32_t)o < (uint32_t)R) return xs[o];
+                                if ((uint32_t)(base + o) < (uint32_t)n) return dep<TX>(x, base + o, status, abort_flag, cap_ns);
+                                return B::val(B::CANON);
                             };
                             int32_t i1 = m.w + li;
                             for (; i1 + v < m.z; i1 += 2 * v) {
@@ -527,19 +544,20 @@ k_sptrsv_blk(const int32_t* __restrict__ chunk_q0, const int32_t* __restrict__ c
                     }
                 } else {
                     // one row longer than a slot: in-block points from global memory
-                    const int4 m = smeta[0];
+                    const int4 m = ok ? smeta[0] : make_int4(0, 0, 0, 0);
                     const int32_t kb = S.e0[e] + m.y;
                     TX acc = 0;
                     for (int32_t i1 = m.w + ct; i1 < m.z; i1 += DDF_BLK_CHAIN_LANES) {
                         const int32_t j = col[kb + i1];
                         const TX xj = (uint32_t)(j - base) < (uint32_t)R ? xs[j - base]
-                                                                         : dep<TX>(x, j, status, abort_flag, cap_ns);
+                                      : (uint32_t)j < (uint32_t)n   ? dep<TX>(x, j, status, abort_flag, cap_ns)
+                                                                    : B::val(B::CANON);
                         acc += ddf_cvt<TX>(val[kb + i1]) * xj;
                     }
                     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
                     if (lane == 0) S.red[warp] = (double)acc;
                     asm volatile("bar.sync 1, %0;" ::"n"(DDF_BLK_CHAIN_LANES) : "memory");
-                    if (ct == 0) {
+                    if (ct == 0 && ok) {
                         TX tot = 0;
                         for (int w = 0; w < BLK_CHAIN; ++w) tot += (TX)S.red[w];
                         TX xr = (xs[m.x] - tot) * sdinv[0];
@@ -584,7 +602,8 @@ ddf_status launch_blocked(ddf_plan_s* p, const TV* val, const TX* dinv, const TX
     if (per_sm < 1) return DDF_ERR_CUDA;
     const int sm = p->sm_count > 0 ? p->sm_count : 152;
     int64_t ctas = std::min<int64_t>((int64_t)p->nblocks, (int64_t)per_sm * sm);
-    kern<<<(unsigned)ctas, threads, smem, s>>>(p->chunk_q0, p->chunk_meta, p->blk_chunk, p->esplit, p->nblocks, R,
+    kern<<<(unsigned)ctas, threads, smem, s>>>(p->chunk_q0, p->chunk_meta, p->blk_chunk, p->esplit, p->n,
+                                               p->nblocks, R,
                                                p->seq, p->starts, p->col, val, dinv, b, x, p->ticket, p->status,
                                                p->opts.spin_cap_ns);
     ddf_count_launch();
