@@ -129,7 +129,8 @@ ddf_status ddf_new_plan(ddf_kind kind, const ddf_opts* o, cudaStream_t s, int32_
 
 // Inspect device CSR arrays the plan takes over (rp, ci and, when present, v);
 // on error everything is released and *out stays NULL.
-ddf_status ddf_finish_plan(ddf_plan_s* p, int32_t* rp, int32_t* ci, double* v, cudaStream_t s, ddf_plan_t* out) {
+ddf_status ddf_finish_plan(ddf_plan_s* p, int32_t* rp, int32_t* ci, double* v, cudaStream_t s, ddf_plan_t* out,
+                           bool borrowed) {
     const ddf_kind kind = p->kind;
     ddf_status st = DDF_OK;
     if (kind == DDF_SPMV && p->nnz > 0 && v == nullptr) {
@@ -158,8 +159,10 @@ ddf_status ddf_finish_plan(ddf_plan_s* p, int32_t* rp, int32_t* ci, double* v, c
     } else {
         // SpTRSV keeps rowptr (as orig_rowptr) and drops the CSR copies
         if (p->orig_rowptr != rp) ddf_free(rp, s);
-        ddf_free(ci, s);
-        ddf_free(v, s);
+        if (!borrowed) {
+            ddf_free(ci, s);
+            ddf_free(v, s);
+        }
     }
     if (!st) st = ddf_make_lowp(p, s);
     if (!st && cudaStreamSynchronize(s) != cudaSuccess) st = DDF_ERR_CUDA;
@@ -235,17 +238,28 @@ ddf_status ddf_inspect(const ddf_csr* A, ddf_kind kind, const ddf_opts* o, ddf_s
     int32_t* rp = nullptr;
     int32_t* ci = nullptr;
     double* v = nullptr;
+    // A SpTRSV plan keeps only rowptr of the input (its columns and values are
+    // re-laid in level order), so device-resident columns and values are read
+    // in place during inspection instead of being copied first.
+    const bool borrow = A->on_device && kind == DDF_SPTRSV;
     st = stage(&rp, A->rowptr, (int64_t)A->n_rows + 1, A->on_device, s);
-    if (!st) st = stage(&ci, A->colidx, A->nnz, A->on_device, s);
-    if (!st && A->values) st = stage(&v, A->values, A->nnz, A->on_device, s);
+    if (borrow) {
+        ci = const_cast<int32_t*>(A->colidx);
+        v = const_cast<double*>(A->values);
+    } else {
+        if (!st) st = stage(&ci, A->colidx, A->nnz, A->on_device, s);
+        if (!st && A->values) st = stage(&v, A->values, A->nnz, A->on_device, s);
+    }
     if (st) {
         ddf_free(rp, s);
-        ddf_free(ci, s);
-        ddf_free(v, s);
+        if (!borrow) {
+            ddf_free(ci, s);
+            ddf_free(v, s);
+        }
         ddf_plan_destroy(p);
         return st;
     }
-    return ddf_finish_plan(p, rp, ci, v, s, out);
+    return ddf_finish_plan(p, rp, ci, v, s, out, borrow);
 }
 
 ddf_status ddf_update_values(ddf_plan_t p, const double* values, int32_t on_device, ddf_stream_t stream) {

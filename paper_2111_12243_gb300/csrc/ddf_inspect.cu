@@ -30,6 +30,8 @@ enum { MK_NONE = -1 };
 // ---------------------------------------------------------------------------
 // validation
 // ---------------------------------------------------------------------------
+// One thread per row; every violation found is reported with atomicMin, so
+// the result is the smallest error code present.
 __global__ void k_validate(int32_t n, int32_t n_cols, int64_t nnz, const int32_t* __restrict__ rp,
                            const int32_t* __restrict__ ci, const double* __restrict__ v, int kind,
                            int32_t* __restrict__ err) {
@@ -60,6 +62,11 @@ __global__ void k_validate(int32_t n, int32_t n_cols, int64_t nnz, const int32_t
         else if (ci[b - 1] != r) atomicMin(err, (int)DDF_ERR_MISSING_DIAG);
         else if (v != nullptr && v[b - 1] == 0.0) atomicMin(err, (int)DDF_ERR_ZERO_DIAG);
     }
+}
+
+__global__ void k_set2(int32_t* __restrict__ a, int32_t v0, int32_t v1) {
+    a[0] = v0;
+    a[1] = v1;
 }
 
 __global__ void k_fill_i32(int32_t* __restrict__ a, int64_t n, int32_t v) {
@@ -461,16 +468,22 @@ __global__ void k_rel_lens(int32_t n, const int32_t* __restrict__ perm, const in
 __global__ void k_rel_gather(int32_t n, const int32_t* __restrict__ perm, const int32_t* __restrict__ rp,
                              const int32_t* __restrict__ ci, const double* __restrict__ vals,
                              const int32_t* __restrict__ st, int32_t* __restrict__ col,
-                             double* __restrict__ val, double* __restrict__ dinv, double* __restrict__ diag) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                             double* __restrict__ val, double* __restrict__ dinv, double* __restrict__ diag,
+                             int lanes) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lg = __ffs(lanes) - 1, li = (int)(t & (lanes - 1));
+    const int64_t q = t >> lg;
     if (q >= n) return;
-    int32_t r = perm[q];
-    int32_t a = rp[r], e = rp[r + 1] - 1, d = st[q];
-    if (col) for (int32_t k = a; k < e; ++k) col[d + (k - a)] = ci[k];
+    const int32_t r = perm[q];
+    const int32_t a = rp[r], e = rp[r + 1] - 1, d = st[q];
+    if (col)
+        for (int32_t k = a + li; k < e; k += lanes) col[d + (k - a)] = ci[k];
     if (vals) {
-        for (int32_t k = a; k < e; ++k) val[d + (k - a)] = vals[k];
-        dinv[q] = 1.0 / vals[e];
-        if (diag) diag[q] = vals[e];
+        for (int32_t k = a + li; k < e; k += lanes) val[d + (k - a)] = vals[k];
+        if (li == 0) {
+            dinv[q] = 1.0 / vals[e];
+            if (diag) diag[q] = vals[e];
+        }
     }
 }
 
@@ -485,18 +498,22 @@ __global__ void k_region_counts(int32_t nparts, const int32_t* __restrict__ pp, 
     rc[l] = (sz + t - 1) / t;
 }
 
+// One thread per region g: its partition is the last p with roff[p] <= g.
 __global__ void k_region_fill(int32_t nparts, const int32_t* __restrict__ pp, int32_t t,
-                              const int64_t* __restrict__ roff, int32_t* __restrict__ ra,
+                              const int64_t* __restrict__ roff, int64_t nreg, int32_t* __restrict__ ra,
                               int32_t* __restrict__ rb, int32_t* __restrict__ rpart) {
-    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= nparts) return;
-    int32_t b0 = pp[l], e0 = pp[l + 1];
-    int64_t o = roff[l];
-    for (int32_t a = b0; a < e0; a += t, ++o) {
-        ra[o] = a;
-        rb[o] = min(a + t, e0);
-        rpart[o] = (int32_t)l;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nreg) return;
+    int32_t lo = 0, hi = nparts - 1;
+    while (lo < hi) {
+        const int32_t mid = lo + ((hi - lo + 1) >> 1);
+        if (roff[mid] <= g) lo = mid;
+        else hi = mid - 1;
     }
+    const int32_t a = pp[lo] + (int32_t)(g - roff[lo]) * t;
+    ra[g] = a;
+    rb[g] = min(a + t, pp[lo + 1]);
+    rpart[g] = lo;
 }
 
 // ---------------------------------------------------------------------------
@@ -508,38 +525,64 @@ struct Feat {
     const int32_t* st;
 };
 
+// v lanes per position: the checks over a row's points are split across the
+// lanes and combined with warp votes inside the group of v lanes.
 __global__ void k_features(int32_t n, const int32_t* __restrict__ seq, const int32_t* __restrict__ st,
                            const int32_t* __restrict__ col, const uint32_t* __restrict__ lsorted,
                            uint8_t* __restrict__ fl, int32_t* __restrict__ sig, int32_t* __restrict__ dF,
-                           int32_t* __restrict__ dG, int32_t* __restrict__ dH) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
-    int32_t a = st[q], L = st[q + 1] - a;
-    const int32_t* h = col + a;
-    uint8_t f = 0;
-    int32_t s = 0;
-    bool ok = true;
-    if (L >= 2) {
-        s = h[1] - h[0];
-        for (int32_t i = 1; i + 1 < L; ++i)
-            if (h[i + 1] - h[i] != s) { ok = false; break; }
+                           int32_t* __restrict__ dG, int32_t* __restrict__ dH, int lanes) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lg = __ffs(lanes) - 1, li = (int)(t & (lanes - 1));
+    const int64_t q = t >> lg;
+    const bool act = q < n;
+    int32_t a = 0, L = 0, s = 0, ap = 0, Lp = 0, d0 = 0;
+    bool link = false;
+    if (act) {
+        a = st[q];
+        L = st[q + 1] - a;
+        link = q > 0 && (lsorted == nullptr || lsorted[q] == lsorted[q - 1]);
+        if (L >= 2) s = col[a + 1] - col[a];
+        if (link) {
+            ap = st[q - 1];
+            Lp = a - ap;
+            if (L == Lp && L > 0) d0 = col[a] - col[ap];
+        }
     }
+    bool ok = true, tr = true;
+    if (act) {
+        const int32_t* h = col + a;
+        for (int32_t i = 1 + li; i + 1 < L; i += lanes)
+            if (h[i + 1] - h[i] != s) {
+                ok = false;
+                break;
+            }
+        if (link && L == Lp) {
+            const int32_t* hp = col + ap;
+            for (int32_t i = 1 + li; i < L; i += lanes)
+                if (h[i] - hp[i] != d0) {
+                    tr = false;
+                    break;
+                }
+        }
+    }
+    // AND over the group of v lanes
+    const unsigned gm = (lanes == 32) ? 0xffffffffu : (((1u << lanes) - 1u) << (threadIdx.x & 31 & ~(lanes - 1)));
+    {
+        const unsigned bo = __ballot_sync(0xffffffffu, !ok), bt = __ballot_sync(0xffffffffu, !tr);
+        ok = (bo & gm) == 0;
+        tr = (bt & gm) == 0;
+    }
+    if (!act || li != 0) return;
+    uint8_t f = 0;
     if (ok) f |= FL_HSTR;
     int32_t df = 0, dg = 0, dh = 0;
-    bool link = q > 0 && (lsorted == nullptr || lsorted[q] == lsorted[q - 1]);
     if (link) {
         f |= FL_LINK;
-        int32_t ap = st[q - 1], Lp = a - ap;
         df = seq ? seq[q] - seq[q - 1] : 1;
         dg = a - ap;
         if (L == Lp) {
             f |= FL_EQLEN;
-            const int32_t* hp = col + ap;
-            bool t = true;
-            int32_t d0 = L > 0 ? h[0] - hp[0] : 0;
-            for (int32_t i = 1; i < L; ++i)
-                if (h[i] - hp[i] != d0) { t = false; break; }
-            if (t) {
+            if (tr) {
                 f |= FL_TRANS;
                 dh = d0;
             }
@@ -1051,6 +1094,15 @@ ddf_status d2h(T* host, const T* dev, int64_t n, cudaStream_t s) {
 
 constexpr int TPB = 256;
 
+// Lanes per row for the per-row inspector kernels: the smallest power of two
+// at least the mean row length, at most 32.
+int lanes_for_mean(int64_t entries, int64_t rows) {
+    const int64_t mean = rows > 0 ? (entries + rows - 1) / rows : 1;
+    int v = 1;
+    while (v < 32 && v < mean) v <<= 1;
+    return v;
+}
+
 void fill_stats(ddf_plan_s* p, const std::vector<dcod>& hc) {
     ddf_plan_stats_t& S = p->stats;
     memset(&S, 0, sizeof(S));
@@ -1104,9 +1156,8 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
         p->depth = n > 0 ? 1 : 0;
         p->npts = p->nnz;
         TRY(ddf_alloc(&p->part_ptr, 2, s));
-        int32_t hp[2] = {0, n};
-        DDF_CUDA_TRY(cudaMemcpyAsync(p->part_ptr, hp, sizeof(hp), cudaMemcpyHostToDevice, s));
-        DDF_CUDA_TRY(cudaStreamSynchronize(s));
+        k_set2<<<1, 1, 0, s>>>(p->part_ptr, 0, n);
+        ddf_count_launch();
     } else {
         // findDependencies: sync-free levels
         int32_t* lev = nullptr;
@@ -1114,7 +1165,7 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
         int32_t* maxlev = nullptr;
         TRY(tmp.get(&lev, n));
         TRY(tmp.get(&tick, 1));
-        TRY(tmp.get(&maxlev, 1));
+        TRY(tmp.get(&maxlev, 2));   // [0] largest level, [1] a copy of the status word
         k_fill_i32<<<ddf_grid(n, TPB, 4096), TPB, 0, s>>>(lev, n, -1);
         ddf_count_launch();
         DDF_CUDA_TRY(cudaMemsetAsync(tick, 0, sizeof(uint32_t), s));
@@ -1126,9 +1177,10 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
             ddf_count_launch();
         }
         DDF_CUDA_TRY(cudaGetLastError());
-        int32_t hmax = 0, hstat = 0;
-        TRY(d2h(&hmax, maxlev, 1, s));
-        TRY(d2h(&hstat, p->status, 1, s));
+        DDF_CUDA_TRY(cudaMemcpyAsync(maxlev + 1, p->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        int32_t hm[2] = {0, 0};
+        TRY(d2h(hm, maxlev, 2, s));
+        const int32_t hmax = hm[0], hstat = hm[1];
         if (hstat) return (ddf_status)hstat;
         p->depth = n > 0 ? hmax + 1 : 0;   // hmax is the largest level
         p->nlevels = p->depth;
@@ -1181,8 +1233,8 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
             ddf_count_launch();
         }
         TRY(ddf_scan_i32_to_i64(lens, st64, n, s));
-        int64_t npts = 0;
-        TRY(d2h(&npts, st64 + n, 1, s));
+        // validated: every row holds exactly one diagonal entry, stored last
+        const int64_t npts = p->nnz - n;
         p->npts = npts;
         TRY(ddf_alloc(&p->starts, (int64_t)n + 1, s));
         k_i64_to_i32<<<ddf_grid(n + 1, TPB, 4096), TPB, 0, s>>>(st64, p->starts, (int64_t)n + 1);
@@ -1194,8 +1246,9 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
         TRY(ddf_alloc(&p->dinv, n, s));
         if (p->opts.store_dtype != DDF_F64) TRY(ddf_alloc(&p->diag, n, s));
         if (n > 0) {
-            k_rel_gather<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, p->seq, rowptr, colidx, values, p->starts,
-                                                        p->col, p->val, p->dinv, p->diag);
+const int gv = lanes_for_mean(npts, n);
+                        k_rel_gather<<<ddf_grid((int64_t)n * gv, TPB), TPB, 0, s>>>(n, p->seq, rowptr, colidx, values, p->starts,
+                                                        p->col, p->val, p->dinv, p->diag, gv);
             ddf_count_launch();
         }
         DDF_CUDA_TRY(cudaGetLastError());
@@ -1228,7 +1281,7 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
     TRY(tmp.get(&rb, nreg));
     TRY(tmp.get(&rpart, nreg));
     if (nparts > 0) {
-        k_region_fill<<<ddf_grid(nparts, TPB), TPB, 0, s>>>(nparts, p->part_ptr, t, roff, ra, rb, rpart);
+        k_region_fill<<<ddf_grid(nreg, TPB), TPB, 0, s>>>(nparts, p->part_ptr, t, roff, nreg, ra, rb, rpart);
         ddf_count_launch();
     }
 
@@ -1242,7 +1295,9 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
     TRY(tmp.get(&dH, n));
     seq = p->seq;
     if (n > 0) {
-        k_features<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, seq, p->starts, p->col, lsorted, fl, sig, dF, dG, dH);
+        const int fv = 1;   // one lane per position measured fastest
+        k_features<<<ddf_grid((int64_t)n * fv, TPB), TPB, 0, s>>>(n, seq, p->starts, p->col, lsorted, fl, sig, dF,
+                                                                 dG, dH, fv);
         ddf_count_launch();
     }
     DDF_CUDA_TRY(cudaGetLastError());
@@ -1309,7 +1364,7 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
     // executor units
     TRY(ddf_build_units(p, s));
     p->stats_ready = 0;
-    DDF_CUDA_TRY(cudaStreamSynchronize(s));
+    DDF_CUDA_TRY(cudaGetLastError());
     return DDF_OK;
 }
 
@@ -1347,10 +1402,15 @@ ddf_status ddf_build_units(ddf_plan_s* p, cudaStream_t s) {
         TRY(ddf_scan_i32_to_i64(c2, o2, ncod, s));
     }
     int64_t tot[3] = {0, 0, 0};
-    TRY(d2h(&tot[0], o0 + ncod, 1, s));
     if (split) {
-        TRY(d2h(&tot[1], o1 + ncod, 1, s));
-        TRY(d2h(&tot[2], o2 + ncod, 1, s));
+        int64_t* t3 = nullptr;
+        TRY(tmp.get(&t3, 3));
+        DDF_CUDA_TRY(cudaMemcpyAsync(t3, o0 + ncod, 8, cudaMemcpyDeviceToDevice, s));
+        DDF_CUDA_TRY(cudaMemcpyAsync(t3 + 1, o1 + ncod, 8, cudaMemcpyDeviceToDevice, s));
+        DDF_CUDA_TRY(cudaMemcpyAsync(t3 + 2, o2 + ncod, 8, cudaMemcpyDeviceToDevice, s));
+        TRY(d2h(tot, t3, 3, s));
+    } else {
+        TRY(d2h(&tot[0], o0 + ncod, 1, s));
     }
     for (int k = 0; k < 3; ++k) {
         p->nunits[k] = tot[k];
@@ -1412,8 +1472,10 @@ ddf_status ddf_gather_values(ddf_plan_s* p, const double* values, cudaStream_t s
     }
     int32_t n = p->n;
     if (n > 0) {
-        k_rel_gather<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, p->seq, p->orig_rowptr, nullptr, values,
-                                                    p->starts, nullptr, p->val, p->dinv, p->diag);
+        const int gv = lanes_for_mean(p->npts, n);
+        k_rel_gather<<<ddf_grid((int64_t)n * gv, TPB), TPB, 0, s>>>(n, p->seq, p->orig_rowptr, nullptr, values,
+                                                                   p->starts, nullptr, p->val, p->dinv, p->diag,
+                                                                   gv);
         ddf_count_launch();
     }
     DDF_CUDA_TRY(cudaGetLastError());

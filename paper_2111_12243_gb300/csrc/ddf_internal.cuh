@@ -187,7 +187,9 @@ ddf_status ddf_build_units(ddf_plan_s* p, cudaStream_t s);
 // ddf_capi.cu
 ddf_status ddf_new_plan(ddf_kind kind, const ddf_opts* o, cudaStream_t s, int32_t n, int32_t n_cols, int64_t nnz,
                         ddf_plan_s** out);
-ddf_status ddf_finish_plan(ddf_plan_s* p, int32_t* rp, int32_t* ci, double* v, cudaStream_t s, ddf_plan_t* out);
+// borrowed: ci / v belong to the caller (read only during this call, not freed)
+ddf_status ddf_finish_plan(ddf_plan_s* p, int32_t* rp, int32_t* ci, double* v, cudaStream_t s, ddf_plan_t* out,
+                           bool borrowed = false);
 // ddf_spmv.cu
 ddf_status ddf_launch_spmv(ddf_plan_s* p, const double* x, double* y, cudaStream_t s);
 ddf_status ddf_launch_spmv_lp(ddf_plan_s* p, const void* x, void* y, int vec_dtype, cudaStream_t s);
