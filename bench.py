@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-critical-path", action="store_true", help="skip the chain solve that measures t_hop")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--coarsen", type=int, default=None,
                     help="SpTRSV rows per block (coarsen_rows; 0 = plain level sets; default: library default)")
@@ -242,9 +243,16 @@ def run_ours(args, rank, world, local_rank):
         cand.append((bd["sptrsv_ms"], f"ddf_sptrsv[{nm}]", bd["sptrsv_bytes"]))
     t_dom, dom, dom_bytes = max(cand)
     achieved = dom_bytes / (t_dom * 1e-3) / 1e9
+    # DRAM bytes per launch: the ratio (dram read + write) / algorithmic bytes
+    # from one ncu capture of the half-scale case, applied to this launch's
+    # algorithmic bytes (the traffic scales with the rows processed).
+    ratio = TRAFFIC_RATIO.get(dom)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
-                "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "traffic": round(ratio * dom_bytes) if ratio else None,
                 "peak_source": f"{peak_kind} copy bandwidth"}
+
+    critical = None if args.no_critical_path else critical_path(ddf, torch, dev, stream, breakdown, hbm)
 
     e2e = None
     if not args.no_e2e:
@@ -260,9 +268,49 @@ def run_ours(args, rank, world, local_rank):
 
     return {
         "value": value, "ms_per_step": ms, "wall_s": wall, "launches": launches, "clocks": clk,
-        "breakdown": breakdown, "roofline": roofline, "e2e": e2e, "exec_bytes_per_step": exec_b,
+        "breakdown": breakdown, "roofline": roofline, "critical_path": critical, "e2e": e2e,
+        "exec_bytes_per_step": exec_b,
         "mixed": mixed, "batched": batched,
     }
+
+
+# (dram__bytes_read.sum + dram__bytes_write.sum) / algorithmic bytes of one
+# launch, from one ncu capture of the half-scale workload (elasticity 32^3
+# nodes: 39.01 MB of DRAM traffic for 36.34 MB of algorithmic bytes).
+TRAFFIC_RATIO = {"ddf_sptrsv[elast3x3_64]": 39.007232e6 / 36341468}
+
+
+def critical_path(ddf, torch, dev, stream, breakdown, hbm, n_chain=8192, reps=5):
+    """The SpTRSV bound max(bytes / HBM bandwidth, depth x t_hop).  t_hop, the
+    cost of one dependency level, is measured on a pure chain (a bidiagonal
+    matrix: n levels of one row each) with the same executor."""
+    ch = synth.chain(n_chain)
+    td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    q = ddf.ddf_inspect(td(ch.rowptr), td(ch.colidx), td(ch.values), ch.n_cols, ddf.DDF_SPTRSV)
+    b = td(synth.uniform_vector(n_chain, 9))
+    x = torch.empty(n_chain, dtype=torch.float64, device=dev)
+    ts = []
+    for i in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ddf.ddf_sptrsv(q, b, x, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i:
+            ts.append(e0.elapsed_time(e1))
+    if ddf.ddf_get_status(q, stream=stream) != 0:
+        return None
+    t_hop = float(np.median(ts)) * 1e3 / n_chain           # us per level
+    out = {"t_hop_us": round(t_hop, 3), "chain_rows": n_chain}
+    for nm, bd in breakdown.items():
+        t_bw = bd["sptrsv_bytes"] / (hbm * 1e9) * 1e6           # us at the measured copy bandwidth
+        t_lat = bd["depth"] * t_hop
+        bound = max(t_bw, t_lat)
+        meas = bd["sptrsv_ms"] * 1e3
+        out[nm] = {"levels": bd["depth"], "bytes_bound_us": round(t_bw, 1), "depth_x_hop_us": round(t_lat, 1),
+                   "bound": "latency" if t_lat >= t_bw else "hbm", "measured_us": round(meas, 1),
+                   "frac_of_bound": round(bound / meas, 3)}
+    return out
 
 
 def run_batch(args, ddf, torch, dev, stream, flush, nrhs=32, reps=5):
@@ -581,6 +629,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single"},
             "frac_of_hbm": round(r["value"] / hbm, 4),
             "roofline": r["roofline"],
+            "critical_path": r["critical_path"],
             "cpu_baseline": cpu,
             "e2e": r["e2e"],
             "gpu_launches": r["launches"],

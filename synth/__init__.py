@@ -19,4 +19,5 @@ from .matrices import (  # noqa: F401
     WORKLOADS,
     batch,
     batch_member,
+    chain,
 )

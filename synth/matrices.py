@@ -300,6 +300,25 @@ def random_pattern(n_rows: int, n_cols: int, density: float, seed: int, *, diag:
     return CSR(n_rows, n_cols, rowptr.astype(np.int32), c.astype(np.int32), v)
 
 
+def chain(n: int) -> CSR:
+    """Lower bidiagonal matrix (1 on the diagonal, -1/2 below): every row reads
+    the one before it, so its dependency graph is one path of n levels."""
+    rp = np.zeros(n + 1, np.int32)
+    if n > 0:
+        rp[1:] = 2 * np.arange(1, n + 1, dtype=np.int32) - 1
+    ci = np.empty(max(2 * n - 1, 0), np.int32)
+    v = np.empty(max(2 * n - 1, 0), np.float64)
+    if n > 0:
+        ci[0] = 0
+        v[0] = 1.0
+        r = np.arange(1, n, dtype=np.int32)
+        ci[1::2] = r - 1
+        ci[2::2] = r
+        v[1::2] = -0.5
+        v[2::2] = 1.0
+    return CSR(n, n, rp, ci, v)
+
+
 def uniform_vector(n: int, seed: int) -> np.ndarray:
     """x ~ U[-1, 1]^n."""
     rng = np.random.Generator(np.random.PCG64(seed))
