@@ -488,17 +488,40 @@ def run_e2e(args, D, ddf, torch, dev, stream, exec_b, world):
         h2d += csr_bytes(a) + csr_bytes(lo) + 8 * a.n_cols + 8 * lo.n_rows
         d2h += 8 * a.n_rows + 8 * lo.n_rows
 
+    # Uploads go on a copy stream in the order the step needs them; the
+    # compute stream waits for each matrix's arrays just before using them, so
+    # the next matrix's copy overlaps this one's inspection and solve.
+    copy = torch.cuda.Stream(device=dev)
+
+    def upload(arrs):
+        return tuple(t.to(dev, non_blocking=True) for t in arrs)
+
     def step():
-        for d, h in zip(D, H):
-            pA = ddf.ddf_inspect(*h["A"], d["a"].n_cols, ddf.DDF_SPMV)
-            x = h["x"].to(dev, non_blocking=True)
+        copy.wait_stream(stream)
+        staged = []
+        with torch.cuda.stream(copy):
+            for h in H:
+                ga = upload(h["A"]) + (h["x"].to(dev, non_blocking=True),)
+                ea = torch.cuda.Event()
+                ea.record(copy)
+                gl = upload(h["L"]) + (h["b"].to(dev, non_blocking=True),)
+                el = torch.cuda.Event()
+                el.record(copy)
+                staged.append((ga, ea, gl, el))
+        for d, h, (ga, ea, gl, el) in zip(D, H, staged):
+            stream.wait_event(ea)
+            for t in ga:
+                t.record_stream(stream)
+            pA = ddf.ddf_inspect(*ga[:3], d["a"].n_cols, ddf.DDF_SPMV)
             y = torch.empty(d["a"].n_rows, dtype=torch.float64, device=dev)
-            ddf.ddf_spmv(pA, x, y)
+            ddf.ddf_spmv(pA, ga[3], y)
             h["y"].copy_(y, non_blocking=True)
-            pL = ddf.ddf_inspect(*h["L"], d["lo"].n_cols, ddf.DDF_SPTRSV)
-            b = h["b"].to(dev, non_blocking=True)
+            stream.wait_event(el)
+            for t in gl:
+                t.record_stream(stream)
+            pL = ddf.ddf_inspect(*gl[:3], d["lo"].n_cols, ddf.DDF_SPTRSV)
             xs = torch.empty(d["lo"].n_rows, dtype=torch.float64, device=dev)
-            ddf.ddf_sptrsv(pL, b, xs)
+            ddf.ddf_sptrsv(pL, gl[3], xs)
             h["xs"].copy_(xs, non_blocking=True)
             pA.destroy()
             pL.destroy()
