@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import threading
 import os
 import statistics
 import subprocess
@@ -50,6 +51,9 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-critical-path", action="store_true", help="skip the chain solve that measures t_hop")
+    ap.add_argument("--serial", action="store_true",
+                    help="run the workload's matrices one after another on one stream (default: one stream "
+                         "and one host thread per matrix)")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--coarsen", type=int, default=None,
                     help="SpTRSV rows per block (coarsen_rows; 0 = plain level sets; default: library default)")
@@ -153,26 +157,48 @@ def run_ours(args, rank, world, local_rank):
 
     opts_L = ddf.ddf_opts_default(coarsen_rows=args.coarsen) if args.coarsen is not None else None
 
+    def one(d, s, e, rec, out, i):
+        """inspect(A), spmv, inspect(L), sptrsv for one matrix on stream s."""
+        torch.cuda.set_device(dev)
+        e[0].record(s)
+        pA = ddf.ddf_inspect(*d["A"], d["a"].n_cols, ddf.DDF_SPMV, None, s)
+        e[1].record(s)
+        ddf.ddf_spmv(pA, d["x"], d["y"], stream=s)
+        e[2].record(s)
+        pL = ddf.ddf_inspect(*d["L"], d["lo"].n_cols, ddf.DDF_SPTRSV, opts_L, s)
+        e[3].record(s)
+        ddf.ddf_sptrsv(pL, d["b"], d["xs"], stream=s)
+        e[4].record(s)
+        if rec:
+            out[i] = (ddf.ddf_plan_stats(pA), ddf.ddf_plan_stats(pL))
+        pA.destroy()
+        pL.destroy()
+
+    side = [torch.cuda.Stream(device=dev) for _ in D]
+
     def step(record):
-        evs = []
-        stats = []
-        for d in D:
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-            e[0].record(stream)
-            pA = ddf.ddf_inspect(*d["A"], d["a"].n_cols, ddf.DDF_SPMV)
-            e[1].record(stream)
-            ddf.ddf_spmv(pA, d["x"], d["y"])
-            e[2].record(stream)
-            pL = ddf.ddf_inspect(*d["L"], d["lo"].n_cols, ddf.DDF_SPTRSV, opts_L)
-            e[3].record(stream)
-            ddf.ddf_sptrsv(pL, d["b"], d["xs"])
-            e[4].record(stream)
-            if record:
-                stats.append((ddf.ddf_plan_stats(pA), ddf.ddf_plan_stats(pL)))
-            pA.destroy()
-            pL.destroy()
-            evs.append(e)
-        return evs, stats
+        """One step; returns per-matrix phase events, plan stats and the step's
+        start / end events on the main stream."""
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in D]
+        stats = [None] * len(D)
+        se = [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+        se[0].record(stream)
+        if args.serial:
+            for i, d in enumerate(D):
+                one(d, stream, evs[i], record, stats, i)
+        else:
+            for s in side:
+                s.wait_stream(stream)
+            th = [threading.Thread(target=one, args=(d, s, evs[i], record, stats, i))
+                  for i, (d, s) in enumerate(zip(D, side))]
+            for t in th:
+                t.start()
+            for t in th:
+                t.join()
+            for s in side:
+                stream.wait_stream(s)
+        se[1].record(stream)
+        return evs, stats, se
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -187,7 +213,7 @@ def run_ours(args, rank, world, local_rank):
     steps = []
     for _ in range(args.steps):
         flush.zero_()
-        steps.append(step(True))
+        steps.append(step(False))
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     if world > 1:
@@ -198,15 +224,25 @@ def run_ours(args, rank, world, local_rank):
     # per-phase times (ms) and bytes
     ph = {(d["name"], p): [] for d in D for p in phases}
     step_ms = []
-    for evs, _ in steps:
-        tot = 0.0
+    for evs, _, se in steps:
         for d, e in zip(D, evs):
             for i, p in enumerate(phases):
-                t = e[i].elapsed_time(e[i + 1])
-                ph[(d["name"], p)].append(t)
-                tot += t
-        step_ms.append(tot)
-    stats = steps[-1][1]
+                ph[(d["name"], p)].append(e[i].elapsed_time(e[i + 1]))
+        step_ms.append(se[0].elapsed_time(se[1]))
+    # plan statistics (a host copy of each plan), from one more step outside
+    # the timed region; the plans are deterministic
+    stats = step(True)[1]
+    serial = None
+    if not args.serial:
+        # the same steps with the matrices one after another, for comparison
+        args.serial = True
+        sms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            sms.append(step(False)[2])
+        torch.cuda.synchronize()
+        args.serial = False
+        serial = float(np.mean([a.elapsed_time(b) for a, b in sms]))
     exec_b = sum(sa["bytes_exec"] + sl["bytes_exec"] for sa, sl in stats)
     ms = float(np.mean(step_ms))
     if world > 1:
@@ -269,6 +305,7 @@ def run_ours(args, rank, world, local_rank):
     return {
         "value": value, "ms_per_step": ms, "wall_s": wall, "launches": launches, "clocks": clk,
         "breakdown": breakdown, "roofline": roofline, "critical_path": critical, "e2e": e2e,
+        "serial_ms_per_step": serial,
         "exec_bytes_per_step": exec_b,
         "mixed": mixed, "batched": batched,
     }
@@ -649,10 +686,15 @@ def main():
             "config": {"workload": "+".join(WORKLOAD), "scale": args.scale,
                        "step": "inspect(A)+spmv+inspect(L)+sptrsv per matrix",
                        "l2": "256 MB flush between steps; inputs larger than L2",
+                       "matrices": "one after another on one stream" if args.serial
+                       else "concurrently, one stream and one host thread per matrix",
                        "parallelism": "replicas" if world > 1 else "single"},
             "frac_of_hbm": round(r["value"] / hbm, 4),
             "roofline": r["roofline"],
             "critical_path": r["critical_path"],
+            "serial": None if r["serial_ms_per_step"] is None else {
+                "ms_per_step": round(r["serial_ms_per_step"], 4),
+                "value": round(r["exec_bytes_per_step"] / (r["serial_ms_per_step"] * 1e-3) / 1e9, 2)},
             "cpu_baseline": cpu,
             "e2e": r["e2e"],
             "gpu_launches": r["launches"],

@@ -15,8 +15,8 @@ void ddf_count_launch(int64_t k) { g_launches.fetch_add(k, std::memory_order_rel
 namespace {
 
 void init_pool_once(int dev) {
-    static bool done[64] = {false};
-    if (dev < 0 || dev >= 64 || done[dev]) return;
+    static std::atomic<bool> done[64];
+    if (dev < 0 || dev >= 64 || done[dev].load()) return;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
         // keep freed plan memory in the process-local pool between inspections
@@ -24,7 +24,7 @@ void init_pool_once(int dev) {
         (void)cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
     (void)cudaGetLastError();
-    done[dev] = true;
+    done[dev].store(true);
 }
 
 void release(ddf_plan_s* p) {

@@ -11,6 +11,7 @@
 #define DDF_MAX_T 512          // largest mining window t (local mask of 512 bits)
 #define DDF_WARPS_PER_CTA 8
 #define DDF_CTA_THREADS (32 * DDF_WARPS_PER_CTA)
+#define DDF_SOLVE_CTAS_PER_SM 2   // resident CTAs per SM of the level-set solve (measured: 1 and 4 are slower)
 // Coarsened solve: a partition is cut into chunks of at most DDF_BLK_ROWS_CAP
 // rows and DDF_BLK_ENT_CAP points, the unit staged into shared memory; a row
 // longer than DDF_BLK_ENT_CAP is a chunk of its own, run from global memory.

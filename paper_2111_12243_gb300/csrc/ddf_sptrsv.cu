@@ -629,6 +629,10 @@ ddf_status launch_solve(ddf_plan_s* p, const TV* val, const TX* dinv, const TX* 
         int per_sm = 0;
         DDF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sptrsv<TV, TX>, DDF_CTA_THREADS, 0));
         if (per_sm < 1) per_sm = 1;
+        // Two CTAs per SM (16 warps) already exceed the units of one level of
+        // the benchmark matrices; the rest of the SM stays free for work on
+        // other streams.
+        if (per_sm > DDF_SOLVE_CTAS_PER_SM) per_sm = DDF_SOLVE_CTAS_PER_SM;
         int64_t ctas = (nu + DDF_WARPS_PER_CTA - 1) / DDF_WARPS_PER_CTA;
         if (ctas > (int64_t)per_sm * sm) ctas = (int64_t)per_sm * sm;
         const dcod* a_cod = p->cod;
