@@ -90,7 +90,7 @@ __global__ void k_i64_to_i32(const int64_t* __restrict__ in, int32_t* __restrict
 // ---------------------------------------------------------------------------
 // findDependencies: level[i] = 1 + max level of its off-diagonal columns
 // ---------------------------------------------------------------------------
-constexpr int LEV_CHUNK = 1024;                               // rows per CTA ticket
+constexpr int LEV_CHUNK = 1024;                               // rows per CTA ticket (a multiple of 1024)
 constexpr int LEV_MAXSEG = 128;                               // longest run one warp takes at once
 
 // Bounded wait on a level written by another CTA: a few immediate polls, then
@@ -199,16 +199,21 @@ k_levels(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ 
     }
     __syncthreads();
     if (w == 0) {
-        // positions of the set bits, in order (one word per lane)
-        const uint32_t m0 = lane < LEV_CHUNK / 32 ? scut[lane] : 0u;
-        const int c = __popc(m0);
+        // positions of the set bits, in order (LEV_WPL consecutive words per lane)
+        constexpr int LEV_WPL = LEV_CHUNK / 1024;
+        int c = 0;
+#pragma unroll
+        for (int i = 0; i < LEV_WPL; ++i) c += __popc(scut[lane * LEV_WPL + i]);
         int pre = c;
         for (int o = 1; o < 32; o <<= 1) {
             const int t = __shfl_up_sync(0xffffffffu, pre, o);
             if (lane >= o) pre += t;
         }
         int k = pre - c;
-        for (uint32_t m = m0; m; m &= m - 1) rstart[k++] = 32 * lane + __ffs(m) - 1;
+#pragma unroll
+        for (int i = 0; i < LEV_WPL; ++i)
+            for (uint32_t m = scut[lane * LEV_WPL + i]; m; m &= m - 1)
+                rstart[k++] = 32 * (lane * LEV_WPL + i) + __ffs(m) - 1;
         if (lane == 31) {
             nruns = pre;
             rstart[pre] = rlen;
