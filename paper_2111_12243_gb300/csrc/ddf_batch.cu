@@ -146,6 +146,8 @@ __device__ __noinline__ TX wait_m(const TX* p, int32_t* status, uint32_t* abort_
     }
 }
 
+constexpr int SM_E = 8;   // points of a row whose loads are in flight together
+
 // Multi-RHS forward substitution over the level-ordered plan.  Each CTA
 // takes the next chunk of upc work units from the ticket when it starts, so
 // every unit it waits on belongs to a CTA that already runs (no co-residency
@@ -192,14 +194,29 @@ k_sptrsm(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64_t 
                     pj = point_col(C, col, i0, kb, i1);
                 }
                 const int32_t cnt = min(32, L - p0);
-                for (int32_t t = 0; t < cnt; ++t) {
-                    const TX a = __shfl_sync(0xffffffffu, pv, t);
-                    const int32_t j = __shfl_sync(0xffffffffu, pj, t);
+                // the loads of up to SM_E points are issued before any is checked,
+                // so one L2 round trip covers them
+                for (int32_t t0 = 0; t0 < cnt; t0 += SM_E) {
+                    typename RBx::U xv[SM_E];
+                    TX av[SM_E];
+                    int32_t jv[SM_E];
+#pragma unroll
+                    for (int e = 0; e < SM_E; ++e) {
+                        const int32_t t = min(t0 + e, cnt - 1);
+                        av[e] = __shfl_sync(0xffffffffu, pv, t);
+                        jv[e] = __shfl_sync(0xffffffffu, pj, t);
+                        xv[e] = (lane < nrhs && t0 + e < cnt) ? RBx::ld(X + (int64_t)jv[e] * nrhs + lane)
+                                                             : (typename RBx::U)0;
+                    }
                     if (lane < nrhs) {
-                        const TX* xp = X + (int64_t)j * nrhs + lane;
-                        typename RBx::U v = RBx::ld(xp);
-                        const TX xj = (v != RBx::SENT) ? RBx::val(v) : wait_m<TX>(xp, status, abort_flag, cap_ns);
-                        acc += a * xj;
+#pragma unroll
+                        for (int e = 0; e < SM_E; ++e) {
+                            if (t0 + e >= cnt) break;
+                            const TX xj = (xv[e] != RBx::SENT)
+                                              ? RBx::val(xv[e])
+                                              : wait_m<TX>(X + (int64_t)jv[e] * nrhs + lane, status, abort_flag, cap_ns);
+                            acc += av[e] * xj;
+                        }
                     }
                 }
             }
