@@ -128,6 +128,17 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def aggregate(ms, exec_b, world, dev):
+    """Whole-job figures over `world` replicas: the step time is the maximum
+    over ranks, the value the bytes of all ranks over that time (GB/s)."""
+    if world > 1:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, exec_b * world / (ms * 1e-3) / 1e9
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2111_12243_gb300 as ddf
@@ -248,12 +259,7 @@ def run_ours(args, rank, world, local_rank):
         args.serial = False
         serial = float(np.mean([a.elapsed_time(b) for a, b in sms]))
     exec_b = sum(sa["bytes_exec"] + sl["bytes_exec"] for sa, sl in stats)
-    ms = float(np.mean(step_ms))
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = exec_b * world / (ms * 1e-3) / 1e9
+    ms, value = aggregate(float(np.mean(step_ms)), exec_b, world, dev)
     hbm, peak_kind = peaks()
 
     breakdown = {}
@@ -581,12 +587,8 @@ def run_e2e(args, D, ddf, torch, dev, stream, exec_b, world):
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
-    ms = float(np.mean(times))
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    return {"value": round(exec_b * world / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+    ms, v = aggregate(float(np.mean(times)), exec_b, world, dev)
+    return {"value": round(v, 2), "unit": "GB/s",
             "ms_per_step": round(ms, 3), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
 
