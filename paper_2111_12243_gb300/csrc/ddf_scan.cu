@@ -79,10 +79,50 @@ __global__ void k_tile_scan(const TIn* __restrict__ in, int64_t n, const int64_t
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = offs[gridDim.x];
 }
 
+// Exclusive scan of at most one tile (n <= SCAN_TILE) by one CTA; out[n] is
+// the total.
+template <typename TIn>
+__global__ void k_scan_one(const TIn* __restrict__ in, int64_t n, int64_t* __restrict__ out) {
+    __shared__ int64_t tile[SCAN_TILE];
+    __shared__ int64_t wsum[SCAN_THREADS / 32];
+    for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS) tile[i] = (i < n) ? (int64_t)in[i] : 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t loc[SCAN_ITEMS];
+    int64_t t = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        loc[j] = t;
+        t += tile[threadIdx.x * SCAN_ITEMS + j];
+    }
+    const int64_t incl = warp_incl_scan(t, lane);
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int64_t v = (lane < SCAN_THREADS / 32) ? wsum[lane] : 0;
+        v = warp_incl_scan(v, lane);
+        if (lane < SCAN_THREADS / 32) wsum[lane] = v;
+    }
+    __syncthreads();
+    const int64_t pre = (incl - t) + (w > 0 ? wsum[w - 1] : 0);
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) tile[threadIdx.x * SCAN_ITEMS + j] = pre + loc[j];
+    __syncthreads();
+    for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS)
+        if (i < n) out[i] = tile[i];
+    if (threadIdx.x == 0) out[n] = wsum[SCAN_THREADS / 32 - 1];
+}
+
 template <typename TIn>
 ddf_status scan_impl(const TIn* in, int64_t* out, int64_t n, cudaStream_t s) {
     if (n <= 0) {
         DDF_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
+        return DDF_OK;
+    }
+    if (n <= SCAN_TILE) {
+        k_scan_one<TIn><<<1, SCAN_THREADS, 0, s>>>(in, n, out);
+        ddf_count_launch();
+        DDF_CUDA_TRY(cudaGetLastError());
         return DDF_OK;
     }
     int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
@@ -94,13 +134,7 @@ ddf_status scan_impl(const TIn* in, int64_t* out, int64_t n, cudaStream_t s) {
     if (st) { ddf_free(sums, s); return st; }
     k_tile_sums<TIn><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, sums);
     ddf_count_launch();
-    if (nb == 1) {
-        // offs = {0, sums[0]}
-        cudaMemsetAsync(offs, 0, sizeof(int64_t), s);
-        cudaMemcpyAsync(offs + 1, sums, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
-    } else {
-        st = scan_impl<int64_t>(sums, offs, nb, s);
-    }
+    st = scan_impl<int64_t>(sums, offs, nb, s);
     if (!st) {
         k_tile_scan<TIn><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, offs, out);
         ddf_count_launch();
