@@ -51,13 +51,17 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-critical-path", action="store_true", help="skip the chain solve that measures t_hop")
-    ap.add_argument("--serial", action="store_true",
-                    help="run the workload's matrices one after another on one stream (default: one stream "
-                         "and one host thread per matrix)")
+    ap.add_argument("--streams", type=int, default=4, choices=[1, 2, 4],
+                    help="1: everything on one stream; 2: one stream and host thread per matrix; "
+                         "4 (default): one per chain, inspect(A)+spmv and inspect(L)+sptrsv of each matrix")
+    ap.add_argument("--serial", action="store_true", help="same as --streams 1")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--coarsen", type=int, default=None,
                     help="SpTRSV rows per block (coarsen_rows; 0 = plain level sets; default: library default)")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.serial:
+        a.streams = 1
+    return a
 
 
 def peaks():
@@ -168,49 +172,70 @@ def run_ours(args, rank, world, local_rank):
 
     opts_L = ddf.ddf_opts_default(coarsen_rows=args.coarsen) if args.coarsen is not None else None
 
-    def one(d, s, e, rec, out, i):
-        """inspect(A), spmv, inspect(L), sptrsv for one matrix on stream s."""
+    def chain_a(d, s, e, rec, out, i):
+        """inspect(A) and spmv of one matrix on stream s (events e[0..2])."""
         torch.cuda.set_device(dev)
         e[0].record(s)
         pA = ddf.ddf_inspect(*d["A"], d["a"].n_cols, ddf.DDF_SPMV, None, s)
         e[1].record(s)
         ddf.ddf_spmv(pA, d["x"], d["y"], stream=s)
         e[2].record(s)
-        pL = ddf.ddf_inspect(*d["L"], d["lo"].n_cols, ddf.DDF_SPTRSV, opts_L, s)
-        e[3].record(s)
-        ddf.ddf_sptrsv(pL, d["b"], d["xs"], stream=s)
-        e[4].record(s)
         if rec:
-            out[i] = (ddf.ddf_plan_stats(pA), ddf.ddf_plan_stats(pL))
+            out[i][0] = ddf.ddf_plan_stats(pA)
         pA.destroy()
+
+    def chain_l(d, s, e, rec, out, i):
+        """inspect(L) and sptrsv of one matrix on stream s (events e[3..5])."""
+        torch.cuda.set_device(dev)
+        e[3].record(s)
+        pL = ddf.ddf_inspect(*d["L"], d["lo"].n_cols, ddf.DDF_SPTRSV, opts_L, s)
+        e[4].record(s)
+        ddf.ddf_sptrsv(pL, d["b"], d["xs"], stream=s)
+        e[5].record(s)
+        if rec:
+            out[i][1] = ddf.ddf_plan_stats(pL)
         pL.destroy()
 
-    # The matrix with the most stored entries has the longest pipeline: its
-    # stream gets the higher priority, the others fill the SMs it leaves idle.
-    big = max(range(len(D)), key=lambda i: D[i]["a"].nnz + D[i]["lo"].nnz)
+    def one(d, s, e, rec, out, i):
+        chain_a(d, s, e, rec, out, i)
+        chain_l(d, s, e, rec, out, i)
+
+    # Larger matrices have the longer pipelines: their streams get the higher
+    # priority, the others fill the SMs they leave idle.
+    order = sorted(range(len(D)), key=lambda i: -(D[i]["a"].nnz + D[i]["lo"].nnz))
     lo_p, hi_p = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
-    side = [torch.cuda.Stream(device=dev, priority=(hi_p if i == big else lo_p)) for i in range(len(D))]
+    prio = {i: (hi_p if k == 0 else lo_p) for k, i in enumerate(order)}
+    side = [torch.cuda.Stream(device=dev, priority=prio[i]) for i in range(len(D))]
+    side_l = [torch.cuda.Stream(device=dev, priority=prio[i]) for i in range(len(D))]
 
     def step(record):
         """One step; returns per-matrix phase events, plan stats and the step's
-        start / end events on the main stream."""
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in D]
-        stats = [None] * len(D)
+        start / end events on the main stream.  --streams 1: matrices and their
+        two chains one after another on the main stream; 2: one stream and host
+        thread per matrix; 4: one per chain (inspect(A) + spmv, and
+        inspect(L) + sptrsv, of each matrix)."""
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in D]
+        stats = [[None, None] for _ in D]
         se = [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
         se[0].record(stream)
-        if args.serial:
+        if args.streams == 1:
             for i, d in enumerate(D):
                 one(d, stream, evs[i], record, stats, i)
         else:
-            for s in side:
+            used = side if args.streams == 2 else side + side_l
+            for s in used:
                 s.wait_stream(stream)
-            th = [threading.Thread(target=one, args=(d, s, evs[i], record, stats, i))
-                  for i, (d, s) in enumerate(zip(D, side))]
+            if args.streams == 2:
+                jobs = [(one, i, side[i]) for i in range(len(D))]
+            else:
+                jobs = [(chain_a, i, side[i]) for i in range(len(D))] + \
+                       [(chain_l, i, side_l[i]) for i in range(len(D))]
+            th = [threading.Thread(target=fn, args=(D[i], s, evs[i], record, stats, i)) for fn, i, s in jobs]
             for t in th:
                 t.start()
             for t in th:
                 t.join()
-            for s in side:
+            for s in used:
                 stream.wait_stream(s)
         se[1].record(stream)
         return evs, stats, se
@@ -239,24 +264,26 @@ def run_ours(args, rank, world, local_rank):
     # per-phase times (ms) and bytes
     ph = {(d["name"], p): [] for d in D for p in phases}
     step_ms = []
+    bounds = {"inspect_spmv": (0, 1), "spmv": (1, 2), "inspect_sptrsv": (3, 4), "sptrsv": (4, 5)}
     for evs, _, se in steps:
         for d, e in zip(D, evs):
-            for i, p in enumerate(phases):
-                ph[(d["name"], p)].append(e[i].elapsed_time(e[i + 1]))
+            for p in phases:
+                a, b = bounds[p]
+                ph[(d["name"], p)].append(e[a].elapsed_time(e[b]))
         step_ms.append(se[0].elapsed_time(se[1]))
     # plan statistics (a host copy of each plan), from one more step outside
     # the timed region; the plans are deterministic
     stats = step(True)[1]
     serial = None
-    if not args.serial:
-        # the same steps with the matrices one after another, for comparison
-        args.serial = True
+    if args.streams != 1:
+        # the same steps with everything on one stream, for comparison
+        keep, args.streams = args.streams, 1
         sms = []
         for _ in range(args.steps):
             flush.zero_()
             sms.append(step(False)[2])
         torch.cuda.synchronize()
-        args.serial = False
+        args.streams = keep
         serial = float(np.mean([a.elapsed_time(b) for a, b in sms]))
     exec_b = sum(sa["bytes_exec"] + sl["bytes_exec"] for sa, sl in stats)
     ms, value = aggregate(float(np.mean(step_ms)), exec_b, world, dev)
@@ -695,8 +722,10 @@ def main():
             "config": {"workload": "+".join(WORKLOAD), "scale": args.scale,
                        "step": "inspect(A)+spmv+inspect(L)+sptrsv per matrix",
                        "l2": "256 MB flush between steps; inputs larger than L2",
-                       "matrices": "one after another on one stream" if args.serial
-                       else "concurrently, one stream and one host thread per matrix",
+                       "streams": {1: "everything on one stream",
+                                   2: "one stream and host thread per matrix",
+                                   4: "one stream and host thread per chain: inspect(A)+spmv, "
+                                      "inspect(L)+sptrsv of each matrix"}[args.streams],
                        "parallelism": "replicas" if world > 1 else "single"},
             "frac_of_hbm": round(r["value"] / hbm, 4),
             "roofline": r["roofline"],
