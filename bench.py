@@ -244,6 +244,23 @@ def run_ours(args, rank, world, local_rank):
         flush.zero_()
         step(False)
     torch.cuda.synchronize()
+    serial = None
+    if args.streams != 1:
+        # the same steps with everything on one stream, for comparison (before
+        # the timed steps, then the concurrent form is warmed up again)
+        keep, args.streams = args.streams, 1
+        step(False)
+        sms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            sms.append(step(False)[2])
+        torch.cuda.synchronize()
+        args.streams = keep
+        serial = float(np.mean([a.elapsed_time(b) for a, b in sms]))
+        for _ in range(args.warmup):
+            flush.zero_()
+            step(False)
+        torch.cuda.synchronize()
     launches0 = ddf.ddf_kernel_launches()
     if world > 1:
         torch.distributed.barrier()
@@ -274,17 +291,7 @@ def run_ours(args, rank, world, local_rank):
     # plan statistics (a host copy of each plan), from one more step outside
     # the timed region; the plans are deterministic
     stats = step(True)[1]
-    serial = None
-    if args.streams != 1:
-        # the same steps with everything on one stream, for comparison
-        keep, args.streams = args.streams, 1
-        sms = []
-        for _ in range(args.steps):
-            flush.zero_()
-            sms.append(step(False)[2])
-        torch.cuda.synchronize()
-        args.streams = keep
-        serial = float(np.mean([a.elapsed_time(b) for a, b in sms]))
+
     exec_b = sum(sa["bytes_exec"] + sl["bytes_exec"] for sa, sl in stats)
     ms, value = aggregate(float(np.mean(step_ms)), exec_b, world, dev)
     hbm, peak_kind = peaks()

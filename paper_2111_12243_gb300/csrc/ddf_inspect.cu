@@ -125,7 +125,7 @@ __device__ int32_t wait_level_smem(volatile int32_t* p, int32_t* status, int64_t
     while (true) {
         int32_t v = *p;
         if (v >= 0) return v;
-        if (++it > 4) __nanosleep(64);
+        if (++it > 32) __nanosleep(32);
         if ((it & 63u) == 0) {
             if (ddf_ld_relaxed_s32(status) != 0) return 0;
             if ((int64_t)(ddf_globaltimer() - t0) > cap_ns) {
