@@ -74,3 +74,48 @@ def test_rejects_damaged_buffers():
     bad[0:8] = b"NOTAPLAN"
     with pytest.raises(ddf.DDFError):
         ddf.ddf_plan_load(bytes(bad), a.n_rows, a.n_cols, ddf.DDF_SPMV)
+
+
+def test_round_trip_coarsened_and_batched():
+    # a coarsened plan carries its block and chunk tables in the buffer
+    lo = synth.lower_triangle(synth.laplacian_7pt(12))
+    o = ddf.ddf_opts_default(coarsen_rows=200)
+    q = ddf.ddf_inspect(dev(lo.rowptr), dev(lo.colidx), dev(lo.values), lo.n_cols, ddf.DDF_SPTRSV, o)
+    q2 = ddf.ddf_plan_load(ddf.ddf_plan_save(q), lo.n_rows, lo.n_cols, ddf.DDF_SPTRSV)
+    assert same_export(q, q2)
+    st, st2 = ddf.ddf_plan_stats(q), ddf.ddf_plan_stats(q2)
+    assert (st2["blocks"], st2["levels"], st2["depth"]) == (st["blocks"], st["levels"], st["depth"])
+    b = dev(synth.uniform_vector(lo.n_rows, 3))
+    x1 = torch.empty(lo.n_rows, dtype=torch.float64, device="cuda")
+    x2 = torch.empty_like(x1)
+    ddf.ddf_sptrsv(q, b, x1)
+    ddf.ddf_sptrsv(q2, b, x2)
+    assert ddf.ddf_get_status(q2) == 0 and torch.equal(x1, x2)
+    # a batched plan solves several right-hand sides after reloading
+    mats = [synth.batch_member(n, k, 7 + i) for i, (n, k) in enumerate([(900, "2d"), (1300, "3d"), (1100, "powerlaw")])]
+    lows = [synth.lower_triangle(m) for m in mats]
+    o32 = ddf.ddf_opts_default(store_dtype=ddf.DDF_F32)
+    p = ddf.ddf_inspect_batch([(dev(m.rowptr), dev(m.colidx), dev(m.values), m.n_cols) for m in lows],
+                              ddf.DDF_SPTRSV, o32)
+    n = sum(m.n_rows for m in lows)
+    p2 = ddf.ddf_plan_load(ddf.ddf_plan_save(p), n, n, ddf.DDF_SPTRSV)
+    assert same_export(p, p2)
+    B = torch.rand((n, 4), dtype=torch.float32, device="cuda")
+    X1 = torch.empty_like(B)
+    X2 = torch.empty_like(B)
+    ddf.ddf_sptrsm(p, B, X1, 4)
+    ddf.ddf_sptrsm(p2, B, X2, 4)
+    assert ddf.ddf_get_status(p2) == 0 and torch.equal(X1, X2)
+
+
+def test_size_query_and_short_buffer():
+    a = synth.laplacian_5pt(10)
+    p = ddf.ddf_inspect(dev(a.rowptr), dev(a.colidx), dev(a.values), a.n_cols, ddf.DDF_SPMV)
+    import ctypes
+    L = ddf.lib()
+    need = ctypes.c_size_t(0)
+    assert L.ddf_plan_save(p.handle, None, ctypes.byref(need)) == 0 and need.value > 0
+    short = ctypes.c_size_t(need.value - 1)
+    buf = ctypes.create_string_buffer(need.value)
+    assert L.ddf_plan_save(p.handle, buf, ctypes.byref(short)) == 1     # too small
+    assert short.value == need.value                                      # reports the size
