@@ -270,11 +270,26 @@ DDF_API ddf_status ddf_plan_export(ddf_plan_t p, int64_t* records, int64_t* ncod
  * on the current device from such a buffer without re-inspection; it checks
  * the header, the sizes and a checksum and returns DDF_ERR_ARG on any
  * mismatch.  The buffer is host-endian.  Both synchronise (save: the plan's
- * stream; load: s).  Load buffers only from ddf_plan_save: the checksum
- * detects corruption, not tampering.
+ * stream; load: s).  The checksum detects corruption, not tampering, so load
+ * also runs ddf_plan_validate on the rebuilt plan and returns its status
+ * (and no plan) when a check fails.
  */
 DDF_API ddf_status ddf_plan_save(ddf_plan_t p, void* buf, size_t* len);
 DDF_API ddf_status ddf_plan_load(const void* buf, size_t len, ddf_stream_t s, ddf_plan_t* out);
+
+/*
+ * Check every index an executor derives from the plan against the arrays it
+ * addresses (Sec. III's access functions: for each codelet the rows f(i0),
+ * the value extents g(i0, i1) and the columns h(i0, i1); the work units; the
+ * level pointers; the coarsened block and chunk tables), and for SpTRSV that
+ * every column names a row below the diagonal that an earlier partition
+ * (Algorithm 1's level or block schedule) solves.  Returns DDF_OK,
+ * DDF_ERR_ARG (a malformed descriptor, unit or table), DDF_ERR_OUT_OF_RANGE
+ * (an index outside its array) or DDF_ERR_NOT_LOWER (a dependency on a row
+ * not yet solved).  Runs on the plan's stream and synchronises it; the plan
+ * is not modified.  Inspection builds plans that pass by construction.
+ */
+DDF_API ddf_status ddf_plan_validate(ddf_plan_t p);
 
 /* Release every device buffer of the plan (stream-ordered on the stream the
  * plan was inspected on).  NULL is ignored. */

@@ -35,7 +35,8 @@ EXPORTS = ("ddf_opts_default", "ddf_inspect", "ddf_update_values", "ddf_spmv", "
            "ddf_get_status", "ddf_plan_stats", "ddf_plan_export", "ddf_plan_destroy",
            "ddf_status_string", "ddf_last_launches", "ddf_kernel_launches",
            "ddf_debug_set_dependency", "ddf_sptrsv_csr_noalloc", "ddf_spmv_lowp", "ddf_sptrsv_refine",
-           "ddf_inspect_batch", "ddf_spmm", "ddf_sptrsm", "ddf_tune", "ddf_plan_save", "ddf_plan_load")
+           "ddf_inspect_batch", "ddf_spmm", "ddf_sptrsm", "ddf_tune", "ddf_plan_save", "ddf_plan_load",
+           "ddf_plan_validate")
 #: rows accepted by ddf_sptrsv_csr_noalloc (the size of its static scratch)
 DDF_NOALLOC_MAX_ROWS = 1 << 20
 DDF_COARSEN_MAX_ROWS = 16384
@@ -129,6 +130,8 @@ def lib():
         for name in ("ddf_inspect", "ddf_update_values", "ddf_spmv", "ddf_sptrsv", "ddf_get_status",
                      "ddf_plan_stats", "ddf_plan_export", "ddf_debug_set_dependency"):
             getattr(L, name).restype = ctypes.c_int
+        L.ddf_plan_validate.argtypes = [P]
+        L.ddf_plan_validate.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -346,6 +349,11 @@ def ddf_plan_load(data: bytes, n_rows: int, n_cols: int, kind: int, stream=None)
     buf = ctypes.create_string_buffer(bytes(data), len(data))
     _check(lib().ddf_plan_load(buf, len(data), _stream(stream), ctypes.byref(h)), "ddf_plan_load")
     return Plan(h, int(kind), int(n_rows), int(n_cols))
+
+
+def ddf_plan_validate(plan: Plan) -> int:
+    """Bounds and dependency checks of a plan on the device; returns the status (0 = valid)."""
+    return int(lib().ddf_plan_validate(plan.handle))
 
 
 def ddf_get_status(plan: Plan, stream=None) -> int:

@@ -17,7 +17,7 @@
 namespace {
 
 constexpr char MAGIC[8] = {'D', 'D', 'F', 'P', 'L', 'A', 'N', '1'};
-constexpr int32_t VERSION = 2;
+constexpr int32_t VERSION = 3;
 
 struct Header {
     char magic[8];
@@ -35,7 +35,7 @@ struct Piece {
 size_t pad8(size_t b) { return (b + 7) & ~(size_t)7; }
 
 uint64_t fnv1a(const unsigned char* p, size_t n) {
-    uint64_t h = 1469598103934665603ull;
+    uint64_t h = 14695981039346656037ull;  // 64-bit FNV offset basis
     for (size_t i = 0; i < n; ++i) {
         h ^= p[i];
         h *= 1099511628211ull;
@@ -233,6 +233,7 @@ ddf_status ddf_plan_load(const void* buf, size_t len, ddf_stream_t stream, ddf_p
         if (!st) st = ddf_alloc(&p->nrm, 2, s);
     }
     if (!st && cudaStreamSynchronize(s) != cudaSuccess) st = DDF_ERR_CUDA;
+    if (!st) st = ddf_plan_validate(p);
     if (st) {
         (void)cudaGetLastError();
         ddf_plan_destroy(p);

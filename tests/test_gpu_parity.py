@@ -318,3 +318,27 @@ def test_full_size_parity(name):
     assert np.linalg.norm(r) <= TOL * np.linalg.norm(b)
     del q
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("name", ["elast_5", "powerlaw_5000", "random_300"])
+@pytest.mark.parametrize("coarsen", [0, 64])
+def test_deterministic_plans_and_results(name, coarsen):
+    """Two inspections of one matrix give identical plans (every exported
+    array), and two executions identical bits: every reduction has a fixed
+    order."""
+    a = SMALL[name]()
+    lo = synth.lower_triangle(a, "unit_dominant" if name.startswith("power") else "keep")
+    x = synth.uniform_vector(a.n_cols, 2)
+    b = synth.uniform_vector(lo.n_rows, 3)
+    exports, ys, xs = [], [], []
+    for _ in range(2):
+        p = inspect(a, 1)
+        q = inspect(lo, 2, coarsen_rows=coarsen)
+        exports.append((ddf.ddf_plan_export(p), ddf.ddf_plan_export(q)))
+        ys.append(run_spmv(p, x, a.n_rows))
+        xs.append(run_sptrsv(q, b, lo.n_rows))
+    for k in ("records", "seq", "part_ptr", "gs"):
+        assert np.array_equal(exports[0][0][k], exports[1][0][k])
+        assert np.array_equal(exports[0][1][k], exports[1][1][k])
+    assert np.array_equal(ys[0].view(np.uint64), ys[1].view(np.uint64))
+    assert np.array_equal(xs[0].view(np.uint64), xs[1].view(np.uint64))
