@@ -34,29 +34,31 @@ enum { MK_NONE = -1 };
 // the result is the smallest error code present.
 __global__ void k_validate(int32_t n, int32_t n_cols, int64_t nnz, const int32_t* __restrict__ rp,
                            const int32_t* __restrict__ ci, const double* __restrict__ v, int kind,
-                           int32_t* __restrict__ err) {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r == 0 && (rp[0] != 0 || (int64_t)rp[n] != nnz)) atomicMin(err, (int)DDF_ERR_UNSORTED);
+                           int32_t* __restrict__ err, int lanes) {
+    // `lanes` consecutive threads per row: lane li checks the entries
+    // a + li, a + li + lanes, ... (coalesced), each against the next entry
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lg = __ffs(lanes) - 1, li = (int)(t & (lanes - 1));
+    const int64_t r = t >> lg;
+    if (t == 0 && (rp[0] != 0 || (int64_t)rp[n] != nnz)) atomicMin(err, (int)DDF_ERR_UNSORTED);
     if (r >= n) return;
-    int32_t a = rp[r], b = rp[r + 1];
+    const int32_t a = rp[r], b = rp[r + 1];
     if (a < 0 || b < a || (int64_t)b > nnz) {
-        atomicMin(err, (int)DDF_ERR_UNSORTED);
+        if (li == 0) atomicMin(err, (int)DDF_ERR_UNSORTED);
         return;
     }
-    int32_t prev = -1;
-    for (int32_t k = a; k < b; ++k) {
-        int32_t c = ci[k];
-        if (c < 0 || c >= n_cols) {
-            atomicMin(err, (int)DDF_ERR_OUT_OF_RANGE);
-            return;
-        }
-        if (c <= prev) {
-            atomicMin(err, (int)DDF_ERR_UNSORTED);
-            return;
-        }
-        prev = c;
+    bool out = false, order = false;
+#pragma unroll 4
+    for (int32_t k = a + li; k < b; k += lanes) {
+        const int32_t c = ci[k];
+        out |= c < 0 || c >= n_cols;
+        if (k + 1 < b) order |= ci[k + 1] <= c;
     }
-    if (kind == DDF_SPTRSV) {
+    // a row with several faults reports the smallest code, as the matrix
+    // does across rows (atomicMin)
+    if (out) atomicMin(err, (int)DDF_ERR_OUT_OF_RANGE);
+    if (order) atomicMin(err, (int)DDF_ERR_UNSORTED);
+    if (kind == DDF_SPTRSV && li == 0 && !out && !order) {
         if (b == a) atomicMin(err, (int)DDF_ERR_MISSING_DIAG);
         else if (ci[b - 1] > r) atomicMin(err, (int)DDF_ERR_NOT_LOWER);
         else if (ci[b - 1] != r) atomicMin(err, (int)DDF_ERR_MISSING_DIAG);
@@ -481,9 +483,12 @@ __global__ void k_rel_gather(int32_t n, const int32_t* __restrict__ perm, const 
     if (q >= n) return;
     const int32_t r = perm[q];
     const int32_t a = rp[r], e = rp[r + 1] - 1, d = st[q];
-    if (col)
+    if (col) {
+#pragma unroll 4
         for (int32_t k = a + li; k < e; k += lanes) col[d + (k - a)] = ci[k];
+    }
     if (vals) {
+#pragma unroll 4
         for (int32_t k = a + li; k < e; k += lanes) val[d + (k - a)] = vals[k];
         if (li == 0) {
             dinv[q] = 1.0 / vals[e];
@@ -1145,7 +1150,9 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
     TRY(tmp.get(&err, 1));
     int32_t big = 0x7fffffff;
     DDF_CUDA_TRY(cudaMemcpyAsync(err, &big, sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    k_validate<<<ddf_grid(n + 1, TPB), TPB, 0, s>>>(n, p->n_cols, p->nnz, rowptr, colidx, values, kind, err);
+    const int gl = lanes_for_mean(p->nnz, n);
+    k_validate<<<ddf_grid(((int64_t)n + 1) * gl, TPB), TPB, 0, s>>>(n, p->n_cols, p->nnz, rowptr, colidx, values,
+                                                                   kind, err, gl);
     ddf_count_launch();
     DDF_CUDA_TRY(cudaGetLastError());
     int32_t herr = 0;
