@@ -572,43 +572,65 @@ def run_e2e(args, D, ddf, torch, dev, stream, exec_b, world):
         h2d += csr_bytes(a) + csr_bytes(lo) + 8 * a.n_cols + 8 * lo.n_rows
         d2h += 8 * a.n_rows + 8 * lo.n_rows
 
-    # Uploads go on a copy stream in the order the step needs them; the
-    # compute stream waits for each matrix's arrays just before using them, so
-    # the next matrix's copy overlaps this one's inspection and solve.
+    # The four chains (inspect(A) + spmv and inspect(L) + sptrsv of each
+    # matrix) run on their own streams and host threads, as in the
+    # device-resident step.  Uploads go on one copy stream, longest chain
+    # first (the L chains, larger matrix first, then the A chains), and each
+    # chain's stream waits only for its own arrays: the long solve chains
+    # start while the remaining arrays are still being copied, instead of
+    # after all of them.
+    opts_L = ddf.ddf_opts_default(coarsen_rows=args.coarsen) if args.coarsen is not None else None
     copy = torch.cuda.Stream(device=dev)
+    size = lambda i: D[i]["a"].nnz + D[i]["lo"].nnz  # noqa: E731
+    by_size = sorted(range(len(D)), key=lambda i: -size(i))
+    order = [("L", i) for i in by_size] + [("A", i) for i in by_size]
+    lo_p, hi_p = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
+    streams = {job: torch.cuda.Stream(device=dev, priority=hi_p if job[1] == by_size[0] else lo_p)
+               for job in order}
 
     def upload(arrs):
         return tuple(t.to(dev, non_blocking=True) for t in arrs)
 
+    def run(kind, i, g, ev):
+        torch.cuda.set_device(dev)
+        s, d, h = streams[(kind, i)], D[i], H[i]
+        s.wait_event(ev)
+        for t in g:
+            t.record_stream(s)
+        with torch.cuda.stream(s):
+            if kind == "A":
+                p = ddf.ddf_inspect(*g[:3], d["a"].n_cols, ddf.DDF_SPMV, None, s)
+                out = torch.empty(d["a"].n_rows, dtype=torch.float64, device=dev)
+                ddf.ddf_spmv(p, g[3], out, stream=s)
+                h["y"].copy_(out, non_blocking=True)
+            else:
+                p = ddf.ddf_inspect(*g[:3], d["lo"].n_cols, ddf.DDF_SPTRSV, opts_L, s)
+                out = torch.empty(d["lo"].n_rows, dtype=torch.float64, device=dev)
+                ddf.ddf_sptrsv(p, g[3], out, stream=s)
+                h["xs"].copy_(out, non_blocking=True)
+            p.destroy()
+
     def step():
         copy.wait_stream(stream)
-        staged = []
+        for s in streams.values():
+            s.wait_stream(stream)
+        jobs = []
         with torch.cuda.stream(copy):
-            for h in H:
-                ga = upload(h["A"]) + (h["x"].to(dev, non_blocking=True),)
-                ea = torch.cuda.Event()
-                ea.record(copy)
-                gl = upload(h["L"]) + (h["b"].to(dev, non_blocking=True),)
-                el = torch.cuda.Event()
-                el.record(copy)
-                staged.append((ga, ea, gl, el))
-        for d, h, (ga, ea, gl, el) in zip(D, H, staged):
-            stream.wait_event(ea)
-            for t in ga:
-                t.record_stream(stream)
-            pA = ddf.ddf_inspect(*ga[:3], d["a"].n_cols, ddf.DDF_SPMV)
-            y = torch.empty(d["a"].n_rows, dtype=torch.float64, device=dev)
-            ddf.ddf_spmv(pA, ga[3], y)
-            h["y"].copy_(y, non_blocking=True)
-            stream.wait_event(el)
-            for t in gl:
-                t.record_stream(stream)
-            pL = ddf.ddf_inspect(*gl[:3], d["lo"].n_cols, ddf.DDF_SPTRSV)
-            xs = torch.empty(d["lo"].n_rows, dtype=torch.float64, device=dev)
-            ddf.ddf_sptrsv(pL, gl[3], xs)
-            h["xs"].copy_(xs, non_blocking=True)
-            pA.destroy()
-            pL.destroy()
+            for kind, i in order:
+                h = H[i]
+                g = upload(h["A"]) + (h["x"].to(dev, non_blocking=True),) if kind == "A" else \
+                    upload(h["L"]) + (h["b"].to(dev, non_blocking=True),)
+                ev = torch.cuda.Event()
+                ev.record(copy)
+                jobs.append((kind, i, g, ev))
+        th = [threading.Thread(target=run, args=job) for job in jobs]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        for s in streams.values():
+            stream.wait_stream(s)
+        stream.wait_stream(copy)
 
     for _ in range(max(1, args.warmup)):
         step()
