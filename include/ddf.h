@@ -316,6 +316,16 @@ DDF_API int64_t ddf_kernel_launches(void);
 DDF_API ddf_status ddf_debug_set_dependency(ddf_plan_t p, int64_t k, int32_t col);
 
 /*
+ * Test hook for failure detection (not part of the method): the library's
+ * next k device allocations succeed and the one after them fails as if the
+ * device were out of memory, so the call making it returns DDF_ERR_OOM after
+ * releasing what it had allocated.  One-shot; k < 0 disarms the hook.
+ * Process-wide, host-side only (no device fault is involved).  Always
+ * returns DDF_OK.
+ */
+DDF_API ddf_status ddf_debug_fail_alloc(int64_t k);
+
+/*
  * Lower-triangular solve that allocates nothing (this entry point has no
  * counterpart in the paper; it serves callers of this library that must not
  * allocate device memory: code running inside a memory-pool or allocator

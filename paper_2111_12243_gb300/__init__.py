@@ -36,7 +36,7 @@ EXPORTS = ("ddf_opts_default", "ddf_inspect", "ddf_update_values", "ddf_spmv", "
            "ddf_status_string", "ddf_last_launches", "ddf_kernel_launches",
            "ddf_debug_set_dependency", "ddf_sptrsv_csr_noalloc", "ddf_spmv_lowp", "ddf_sptrsv_refine",
            "ddf_inspect_batch", "ddf_spmm", "ddf_sptrsm", "ddf_tune", "ddf_plan_save", "ddf_plan_load",
-           "ddf_plan_validate")
+           "ddf_plan_validate", "ddf_debug_fail_alloc")
 #: rows accepted by ddf_sptrsv_csr_noalloc (the size of its static scratch)
 DDF_NOALLOC_MAX_ROWS = 1 << 20
 DDF_COARSEN_MAX_ROWS = 16384
@@ -132,6 +132,8 @@ def lib():
             getattr(L, name).restype = ctypes.c_int
         L.ddf_plan_validate.argtypes = [P]
         L.ddf_plan_validate.restype = ctypes.c_int
+        L.ddf_debug_fail_alloc.argtypes = [I64]
+        L.ddf_debug_fail_alloc.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -402,6 +404,11 @@ def ddf_kernel_launches() -> int:
 
 def ddf_debug_set_dependency(plan: Plan, k: int, col: int):
     _check(lib().ddf_debug_set_dependency(plan.handle, int(k), int(col)), "ddf_debug_set_dependency")
+
+
+def ddf_debug_fail_alloc(k: int):
+    """Make the library's device allocation after the next k fail with DDF_ERR_OOM (k < 0: off)."""
+    lib().ddf_debug_fail_alloc(int(k))
 
 
 def ddf_sptrsv_csr_noalloc(rowptr, colidx, values, b, x, spin_cap_ns: int = 2_000_000_000,

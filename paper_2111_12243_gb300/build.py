@@ -62,7 +62,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
         objs = list(ex.map(compile_one, _sources()))
     tmp = LIB + f".tmp.{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", *objs, "-o", tmp]
+    cmd = [nvcc, *ARCH, "-shared", *objs, "-o", tmp, "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

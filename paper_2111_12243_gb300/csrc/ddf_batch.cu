@@ -304,6 +304,7 @@ extern "C" {
 
 ddf_status ddf_inspect_batch(const ddf_csr* mats, int32_t count, ddf_kind kind, const ddf_opts* o,
                              ddf_stream_t stream, ddf_plan_t* out) {
+    ddf_nvtx_range nvtx_("ddf_inspect_batch");
     if (!out) return DDF_ERR_ARG;
     *out = nullptr;
     if (!mats || count < 1 || (kind != DDF_SPMV && kind != DDF_SPTRSV)) return DDF_ERR_ARG;
@@ -378,6 +379,7 @@ ddf_status ddf_inspect_batch(const ddf_csr* mats, int32_t count, ddf_kind kind, 
 }
 
 ddf_status ddf_spmm(ddf_plan_t p, const void* X, void* Y, int32_t nrhs, ddf_dtype dtype, ddf_stream_t stream) {
+    ddf_nvtx_range nvtx_("ddf_spmm");
     ddf_status st = check_multi(p, X, Y, nrhs, dtype);
     if (st) return st;
     if (p->kind != DDF_SPMV) return DDF_ERR_WRONG_KIND;
@@ -389,6 +391,7 @@ ddf_status ddf_spmm(ddf_plan_t p, const void* X, void* Y, int32_t nrhs, ddf_dtyp
 }
 
 ddf_status ddf_sptrsm(ddf_plan_t p, const void* B, void* X, int32_t nrhs, ddf_dtype dtype, ddf_stream_t stream) {
+    ddf_nvtx_range nvtx_("ddf_sptrsm");
     ddf_status st = check_multi(p, B, X, nrhs, dtype);
     if (st) return st;
     if (p->kind != DDF_SPTRSV) return DDF_ERR_WRONG_KIND;
@@ -404,6 +407,7 @@ ddf_status ddf_sptrsm(ddf_plan_t p, const void* B, void* X, int32_t nrhs, ddf_dt
 
 ddf_status ddf_tune(ddf_plan_t p, const void* in, void* out, int32_t nrhs, ddf_dtype dtype, ddf_stream_t stream,
                     int32_t* best_unit_nnz) {
+    ddf_nvtx_range nvtx_("ddf_tune");
     ddf_status st = check_multi(p, in, out, nrhs, dtype);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;

@@ -7,10 +7,26 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ddf_internal.cuh"
 
 static std::atomic<int64_t> g_launches{0};
 void ddf_count_launch(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// ddf_debug_fail_alloc: allocations still to succeed before one fails (-1: off)
+static std::atomic<int64_t> g_alloc_countdown{-1};
+
+bool ddf_alloc_injected_failure() {
+    int64_t c = g_alloc_countdown.load(std::memory_order_relaxed);
+    while (c >= 0) {
+        if (g_alloc_countdown.compare_exchange_weak(c, c - 1, std::memory_order_relaxed)) return c == 0;
+    }
+    return false;
+}
+
+ddf_nvtx_range::ddf_nvtx_range(const char* name) { nvtxRangePushA(name); }
+ddf_nvtx_range::~ddf_nvtx_range() { nvtxRangePop(); }
 
 namespace {
 
@@ -214,6 +230,7 @@ const char* ddf_status_string(ddf_status st) {
 
 ddf_status ddf_inspect(const ddf_csr* A, ddf_kind kind, const ddf_opts* o, ddf_stream_t stream,
                        ddf_plan_t* out) {
+    ddf_nvtx_range nvtx_("ddf_inspect");
     if (!out) return DDF_ERR_ARG;
     *out = nullptr;
     if (!A || (kind != DDF_SPMV && kind != DDF_SPTRSV)) return DDF_ERR_ARG;
@@ -263,6 +280,7 @@ ddf_status ddf_inspect(const ddf_csr* A, ddf_kind kind, const ddf_opts* o, ddf_s
 }
 
 ddf_status ddf_update_values(ddf_plan_t p, const double* values, int32_t on_device, ddf_stream_t stream) {
+    ddf_nvtx_range nvtx_("ddf_update_values");
     if (!p || (!values && p->nnz > 0)) return DDF_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     double* v = nullptr;
@@ -294,6 +312,7 @@ ddf_status ddf_update_values(ddf_plan_t p, const double* values, int32_t on_devi
 }
 
 ddf_status ddf_spmv(ddf_plan_t p, const double* x, double* y, ddf_stream_t stream) {
+    ddf_nvtx_range nvtx_("ddf_spmv");
     if (!p) return DDF_ERR_ARG;
     if (p->kind != DDF_SPMV) return DDF_ERR_WRONG_KIND;
     if ((p->n > 0 && !y) || (p->n_cols > 0 && !x) || (p->nnz > 0 && !p->has_values)) return DDF_ERR_ARG;
@@ -305,6 +324,7 @@ ddf_status ddf_spmv(ddf_plan_t p, const double* x, double* y, ddf_stream_t strea
 }
 
 ddf_status ddf_sptrsv(ddf_plan_t p, const double* b, double* x, ddf_stream_t stream) {
+    ddf_nvtx_range nvtx_("ddf_sptrsv");
     if (!p) return DDF_ERR_ARG;
     if (p->kind != DDF_SPTRSV) return DDF_ERR_WRONG_KIND;
     if (p->n > 0 && (!b || !x || !p->has_values)) return DDF_ERR_ARG;
@@ -318,6 +338,7 @@ ddf_status ddf_sptrsv(ddf_plan_t p, const double* b, double* x, ddf_stream_t str
 }
 
 ddf_status ddf_spmv_lowp(ddf_plan_t p, const void* x, void* y, ddf_dtype vec_dtype, ddf_stream_t stream) {
+    ddf_nvtx_range nvtx_("ddf_spmv_lowp");
     if (!p) return DDF_ERR_ARG;
     if (p->kind != DDF_SPMV) return DDF_ERR_WRONG_KIND;
     if (p->vdtype != DDF_F32 && p->vdtype != DDF_BF16) return DDF_ERR_ARG;
@@ -332,6 +353,7 @@ ddf_status ddf_spmv_lowp(ddf_plan_t p, const void* x, void* y, ddf_dtype vec_dty
 
 ddf_status ddf_sptrsv_refine(ddf_plan_t p, const double* b, double* x, double tol, int32_t max_iter,
                              ddf_stream_t stream, int32_t* iters, double* relres) {
+    ddf_nvtx_range nvtx_("ddf_sptrsv_refine");
     if (!p) return DDF_ERR_ARG;
     if (p->kind != DDF_SPTRSV) return DDF_ERR_WRONG_KIND;
     if (p->vdtype != DDF_F32 && p->vdtype != DDF_BF16) return DDF_ERR_ARG;
@@ -426,6 +448,11 @@ void ddf_plan_destroy(ddf_plan_t p) {
 int32_t ddf_last_launches(ddf_plan_t p) { return p ? p->last_launches : 0; }
 
 int64_t ddf_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+ddf_status ddf_debug_fail_alloc(int64_t k) {
+    g_alloc_countdown.store(k < 0 ? -1 : k, std::memory_order_relaxed);
+    return DDF_OK;
+}
 
 ddf_status ddf_debug_set_dependency(ddf_plan_t p, int64_t k, int32_t col) {
     if (!p || p->kind != DDF_SPTRSV || k < 0 || k >= p->npts || col < 0 || col >= p->n) return DDF_ERR_ARG;

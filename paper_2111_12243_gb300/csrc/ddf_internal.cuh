@@ -205,11 +205,23 @@ ddf_status ddf_refine(ddf_plan_s* p, const double* b, double* x, double tol, int
 // process-wide count of kernel launches (ddf_capi.cu)
 void ddf_count_launch(int64_t k = 1);
 
+// test hook of ddf_debug_fail_alloc (ddf_capi.cu): true for the one device
+// allocation that is to fail as if the device were out of memory
+bool ddf_alloc_injected_failure();
+
+// NVTX range around an entry point (header-only NVTX 3: a no-op unless a
+// profiling tool is attached)
+struct ddf_nvtx_range {
+    explicit ddf_nvtx_range(const char* name);
+    ~ddf_nvtx_range();
+};
+
 // device allocation helpers (stream-ordered)
 template <typename T>
 static inline ddf_status ddf_alloc(T** ptr, int64_t count, cudaStream_t s) {
     *ptr = nullptr;
     if (count <= 0) return DDF_OK;
+    if (ddf_alloc_injected_failure()) return DDF_ERR_OOM;
     cudaError_t e = cudaMallocAsync((void**)ptr, (size_t)count * sizeof(T), s);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();

@@ -166,6 +166,7 @@ extern "C" ddf_status ddf_sptrsv_csr_noalloc(int32_t n, int64_t nnz, const int32
                                              const int32_t* colidx, const double* values,
                                              const double* b, double* x, int64_t spin_cap_ns,
                                              ddf_stream_t stream) {
+    ddf_nvtx_range nvtx_("ddf_sptrsv_csr_noalloc");
     if (n < 0 || nnz < 0 || nnz > 0x7fffffffll || spin_cap_ns <= 0) return DDF_ERR_ARG;
     if (n > DDF_NOALLOC_MAX_ROWS) return DDF_ERR_TOO_LARGE;
     if (n == 0) return DDF_OK;

@@ -123,6 +123,7 @@ size_t total_bytes(const std::vector<Piece>& v) {
 extern "C" {
 
 ddf_status ddf_plan_save(ddf_plan_t p, void* buf, size_t* len) {
+    ddf_nvtx_range nvtx_("ddf_plan_save");
     if (!p || !len) return DDF_ERR_ARG;
     Header h = header_of(p);
     void** slots[24];
@@ -153,6 +154,7 @@ ddf_status ddf_plan_save(ddf_plan_t p, void* buf, size_t* len) {
 }
 
 ddf_status ddf_plan_load(const void* buf, size_t len, ddf_stream_t stream, ddf_plan_t* out) {
+    ddf_nvtx_range nvtx_("ddf_plan_load");
     if (!out) return DDF_ERR_ARG;
     *out = nullptr;
     if (!buf || len < pad8(sizeof(Header)) + sizeof(uint64_t)) return DDF_ERR_ARG;
@@ -215,7 +217,7 @@ ddf_status ddf_plan_load(const void* buf, size_t len, ddf_stream_t stream, ddf_p
         if (b > 0) {
             void* d = nullptr;
             // 16 spare bytes: val / col / val_lp are staged by 16-byte-granular bulk copies
-            if (cudaMallocAsync(&d, b + 16, s) != cudaSuccess) {
+            if (ddf_alloc_injected_failure() || cudaMallocAsync(&d, b + 16, s) != cudaSuccess) {
                 (void)cudaGetLastError();
                 st = DDF_ERR_OOM;
                 break;

@@ -178,6 +178,7 @@ __global__ void k_check_chunks(int32_t n, int32_t R, int32_t nblocks, int64_t nc
 extern "C" {
 
 ddf_status ddf_plan_validate(ddf_plan_t p) {
+    ddf_nvtx_range nvtx_("ddf_plan_validate");
     if (!p) return DDF_ERR_ARG;
     cudaStream_t s = p->stream;
     const int32_t n = p->n;
