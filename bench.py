@@ -225,11 +225,13 @@ def run_ours(args, rank, world, local_rank):
             used = side if args.streams == 2 else side + side_l
             for s in used:
                 s.wait_stream(stream)
+            # host threads start one after another, each some 0.1-0.7 ms after
+            # the last: the longest chains go first (the L chains, larger matrix
+            # first, then the A chains)
             if args.streams == 2:
-                jobs = [(one, i, side[i]) for i in range(len(D))]
+                jobs = [(one, i, side[i]) for i in order]
             else:
-                jobs = [(chain_a, i, side[i]) for i in range(len(D))] + \
-                       [(chain_l, i, side_l[i]) for i in range(len(D))]
+                jobs = [(chain_l, i, side_l[i]) for i in order] + [(chain_a, i, side[i]) for i in order]
             th = [threading.Thread(target=fn, args=(D[i], s, evs[i], record, stats, i)) for fn, i, s in jobs]
             for t in th:
                 t.start()
@@ -282,12 +284,18 @@ def run_ours(args, rank, world, local_rank):
     ph = {(d["name"], p): [] for d in D for p in phases}
     step_ms = []
     bounds = {"inspect_spmv": (0, 1), "spmv": (1, 2), "inspect_sptrsv": (3, 4), "sptrsv": (4, 5)}
+    # timeline of the step: start and end of each chain after the step's start event
+    tl = {(d["name"], c): [] for d in D for c in ("A", "L")}
     for evs, _, se in steps:
         for d, e in zip(D, evs):
             for p in phases:
                 a, b = bounds[p]
                 ph[(d["name"], p)].append(e[a].elapsed_time(e[b]))
+            tl[(d["name"], "A")].append((se[0].elapsed_time(e[0]), se[0].elapsed_time(e[2])))
+            tl[(d["name"], "L")].append((se[0].elapsed_time(e[3]), se[0].elapsed_time(e[5])))
         step_ms.append(se[0].elapsed_time(se[1]))
+    timeline = {f"{nm}/{c}": [round(float(np.mean([t[0] for t in v])), 3), round(float(np.mean([t[1] for t in v])), 3)]
+                for (nm, c), v in tl.items()}
     # plan statistics (a host copy of each plan), from one more step outside
     # the timed region; the plans are deterministic
     stats = step(True)[1]
@@ -352,7 +360,7 @@ def run_ours(args, rank, world, local_rank):
     return {
         "value": value, "ms_per_step": ms, "wall_s": wall, "launches": launches, "clocks": clk,
         "breakdown": breakdown, "roofline": roofline, "critical_path": critical, "e2e": e2e,
-        "serial_ms_per_step": serial,
+        "serial_ms_per_step": serial, "timeline": timeline,
         "exec_bytes_per_step": exec_b,
         "mixed": mixed, "batched": batched,
     }
@@ -767,6 +775,9 @@ def main():
             "gpu_launches": r["launches"],
             "clocks": r["clocks"],
             "breakdown": r["breakdown"],
+            # [start, end] of each chain (A: inspect(A) + spmv, L: inspect(L) +
+            # sptrsv) in ms after the step's start event, mean over the timed steps
+            "timeline_ms": r["timeline"],
             "mixed_precision": r["mixed"],
             "batched": r["batched"],
             "exec_bytes_per_step": r["exec_bytes_per_step"],
