@@ -292,7 +292,8 @@ DDF_API ddf_status ddf_plan_load(const void* buf, size_t len, ddf_stream_t s, dd
 DDF_API ddf_status ddf_plan_validate(ddf_plan_t p);
 
 /* Release every device buffer of the plan (stream-ordered on the stream the
- * plan was inspected on).  NULL is ignored. */
+ * plan was inspected on, after the work queued there; the call does not
+ * wait for it).  NULL is ignored. */
 DDF_API void ddf_plan_destroy(ddf_plan_t p);
 
 /* Static description of a status code. */

@@ -439,8 +439,9 @@ ddf_status ddf_plan_export(ddf_plan_t p, int64_t* records, int64_t* ncodelets, i
 
 void ddf_plan_destroy(ddf_plan_t p) {
     if (!p) return;
+    // the frees are ordered on the plan's stream after the work queued there
+    // (work that may still be running), so nothing waits here
     release(p);
-    (void)cudaStreamSynchronize(p->stream);
     (void)cudaGetLastError();
     delete p;
 }
