@@ -1119,6 +1119,10 @@ int lanes_for_mean(int64_t entries, int64_t rows, int cap = 32) {
 // 2.37-2.46 -> 2.21 ms against 32 lanes per row).
 constexpr int REL_GATHER_MAX_LANES = 8;
 
+// CSR validation: at most 4 lanes per row (inspect(L) of elasticity 64^3:
+// 2.22 ms with 32 lanes per row, 2.10 ms with 4, 2.14 ms with one)
+constexpr int VALIDATE_MAX_LANES = 4;
+
 void fill_stats(ddf_plan_s* p, const std::vector<dcod>& hc) {
     ddf_plan_stats_t& S = p->stats;
     memset(&S, 0, sizeof(S));
@@ -1156,7 +1160,7 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
     TRY(tmp.get(&err, 1));
     int32_t big = 0x7fffffff;
     DDF_CUDA_TRY(cudaMemcpyAsync(err, &big, sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    const int gl = lanes_for_mean(p->nnz, n);
+    const int gl = lanes_for_mean(p->nnz, n, VALIDATE_MAX_LANES);
     k_validate<<<ddf_grid(((int64_t)n + 1) * gl, TPB), TPB, 0, s>>>(n, p->n_cols, p->nnz, rowptr, colidx, values,
                                                                    kind, err, gl);
     ddf_count_launch();
