@@ -110,7 +110,13 @@ typedef struct {
                                then level order.  A coarsened plan is solved one block per
                                CTA, dependencies inside a block through shared memory
                                (default DDF_COARSEN_DEFAULT_ROWS = 0: level sets)             */
-    int32_t reserved[7];
+    int32_t lower_of_input; /* SpTRSV: 0 (default) = the input is the lower-triangular L; 1 =
+                               the input is a square matrix A and L is its lower triangle,
+                               each row's entries with column <= row (a prefix of the sorted
+                               row), read in place without a copy.  Every row of A must then
+                               hold its diagonal.  ddf_update_values takes A's values.  Must
+                               be 0 for SpMV                                                   */
+    int32_t reserved[6];
 } ddf_opts;
 
 #define DDF_COARSEN_MAX_ROWS 16384

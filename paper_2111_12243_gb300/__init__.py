@@ -64,7 +64,7 @@ class ddf_opts(ctypes.Structure):
                 ("w_op", ctypes.c_int64), ("w_codelet", ctypes.c_int64), ("w_index", ctypes.c_int64),
                 ("spin_cap_ns", ctypes.c_int64), ("unit_nnz", ctypes.c_int32),
                 ("store_dtype", ctypes.c_int32), ("coarsen_rows", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("lower_of_input", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class ddf_plan_stats_t(ctypes.Structure):

@@ -52,6 +52,7 @@ void release(ddf_plan_s* p) {
     ddf_free(p->part_ptr, s);
     ddf_free(p->dinv, s);
     ddf_free(p->orig_rowptr, s);
+    ddf_free(p->orig_rowend, s);
     ddf_free(p->cod, s);
     for (int k = 0; k < 3; ++k) ddf_free(p->units[k], s);
     ddf_free(p->status, s);
@@ -79,6 +80,7 @@ ddf_status check_opts(const ddf_opts* o) {
     if (o->spin_cap_ns <= 0 || o->unit_nnz < 1) return DDF_ERR_ARG;
     if (o->store_dtype != DDF_F64 && o->store_dtype != DDF_F32 && o->store_dtype != DDF_BF16) return DDF_ERR_ARG;
     if (o->coarsen_rows < 0 || o->coarsen_rows > DDF_COARSEN_MAX_ROWS) return DDF_ERR_ARG;
+    if (o->lower_of_input != 0 && o->lower_of_input != 1) return DDF_ERR_ARG;
     return DDF_OK;
 }
 
@@ -93,10 +95,11 @@ ddf_status stage(T** dst, const T* src, int64_t n, int on_device, cudaStream_t s
     return DDF_OK;
 }
 
-__global__ void k_check_diag(int32_t n, const int32_t* __restrict__ rp, const double* __restrict__ v,
+// re[r]: end of row r of L (its diagonal is the entry before it)
+__global__ void k_check_diag(int32_t n, const int32_t* __restrict__ re, const double* __restrict__ v,
                              int32_t* __restrict__ bad) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < n && v[rp[r + 1] - 1] == 0.0) atomicExch(bad, 1);
+    if (r < n && v[re[r] - 1] == 0.0) atomicExch(bad, 1);
 }
 
 }  // namespace
@@ -110,6 +113,7 @@ ddf_status ddf_new_plan(ddf_kind kind, const ddf_opts* o, cudaStream_t s, int32_
     else ddf_opts_default(&opts);
     ddf_status st = check_opts(&opts);
     if (st) return st;
+    if (kind == DDF_SPMV && opts.lower_of_input) return DDF_ERR_ARG;
     ddf_plan_s* p = new (std::nothrow) ddf_plan_s();
     if (!p) return DDF_ERR_OOM;
     memset(p, 0, sizeof(*p));
@@ -297,7 +301,8 @@ ddf_status ddf_update_values(ddf_plan_t p, const double* values, int32_t on_devi
         if (!st) {
             int32_t hb = 0;
             cudaMemsetAsync(bad, 0, sizeof(int32_t), s);
-            k_check_diag<<<ddf_grid(p->n, 256), 256, 0, s>>>(p->n, p->orig_rowptr, src, bad);
+            const int32_t* re = p->orig_rowend ? p->orig_rowend : p->orig_rowptr + 1;
+            k_check_diag<<<ddf_grid(p->n, 256), 256, 0, s>>>(p->n, re, src, bad);
             ddf_count_launch();
             cudaMemcpyAsync(&hb, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
             if (cudaStreamSynchronize(s) != cudaSuccess) st = DDF_ERR_CUDA;

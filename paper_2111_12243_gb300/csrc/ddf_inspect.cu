@@ -66,6 +66,30 @@ __global__ void k_validate(int32_t n, int32_t n_cols, int64_t nnz, const int32_t
     }
 }
 
+// lower_of_input: the end of the lower part of each row of a validated
+// square matrix (its columns increase, so the part is a prefix: the first
+// entry with a column above the row ends it), and that part's diagonal
+// checks.  Rows that failed validation get an empty part.
+__global__ void k_lower_end(int32_t n, int64_t nnz, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const double* __restrict__ v, int32_t* __restrict__ re, int32_t* __restrict__ err) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int32_t a = rp[r], b = rp[r + 1];
+    if (a < 0 || b < a || (int64_t)b > nnz) {
+        re[r] = a < 0 ? 0 : a;
+        return;
+    }
+    int32_t lo = a, hi = b;   // first k in [a, b) with ci[k] > r, else b
+    while (lo < hi) {
+        const int32_t mid = lo + ((hi - lo) >> 1);
+        if (ci[mid] > r) hi = mid;
+        else lo = mid + 1;
+    }
+    re[r] = lo;
+    if (lo == a || ci[lo - 1] != r) atomicMin(err, (int)DDF_ERR_MISSING_DIAG);
+    else if (v != nullptr && v[lo - 1] == 0.0) atomicMin(err, (int)DDF_ERR_ZERO_DIAG);
+}
+
 __global__ void k_set2(int32_t* __restrict__ a, int32_t v0, int32_t v1) {
     a[0] = v0;
     a[1] = v1;
@@ -171,8 +195,8 @@ __device__ __forceinline__ void lev_prefetch(int32_t a, int32_t b, int lane, int
 }
 
 __global__ void __launch_bounds__(32 * LEV_WARPS)
-k_levels(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int32_t* lev,
-         uint32_t* ticket, int32_t* maxlev, int32_t* status, int64_t cap_ns) {
+k_levels(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ re, const int32_t* __restrict__ ci,
+         int32_t* lev, uint32_t* ticket, int32_t* maxlev, int32_t* status, int64_t cap_ns) {
     __shared__ int32_t chunk, nruns, next;
     __shared__ int32_t wmax[LEV_WARPS];
     __shared__ int32_t slev[LEV_CHUNK];
@@ -193,7 +217,7 @@ k_levels(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ 
         bool cut = false;
         if (o < rlen) {
             const int64_t r = base + o;
-            const int32_t e = rp[r + 1] - 1;   // the diagonal is last
+            const int32_t e = re[r] - 1;   // the diagonal is last
             cut = (o % LEV_MAXSEG) == 0 || !(e > rp[r] && ci[e - 1] == (int32_t)(r - 1));
         }
         const unsigned m = __ballot_sync(0xffffffffu, cut);
@@ -237,7 +261,7 @@ k_levels(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ 
             int32_t ra_l = 0, rb_l = 0;
             if (lane < cnt) {
                 ra_l = rp[r0 + lane];
-                rb_l = rp[r0 + lane + 1] - 1;   // the diagonal is last: not a dependency
+                rb_l = re[r0 + lane] - 1;   // the diagonal is last: not a dependency
             }
             int32_t cj[LEV_PF], cl[LEV_PF];
             {
@@ -464,16 +488,19 @@ __global__ void k_blk_chunk(int32_t nblocks, const int32_t* __restrict__ bp, con
 // ---------------------------------------------------------------------------
 // SpTRSV relayout: off-diagonal columns and values of the rows in level order
 // ---------------------------------------------------------------------------
+// rp[r] .. re[r]: row r of L, its diagonal last (re = rp + 1 when the input is
+// L itself; the end of the lower part of each row when L is read from A)
 __global__ void k_rel_lens(int32_t n, const int32_t* __restrict__ perm, const int32_t* __restrict__ rp,
-                           int32_t* __restrict__ lens) {
+                           const int32_t* __restrict__ re, int32_t* __restrict__ lens) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     int32_t r = perm[q];
-    lens[q] = rp[r + 1] - rp[r] - 1;
+    lens[q] = re[r] - rp[r] - 1;
 }
 
 __global__ void k_rel_gather(int32_t n, const int32_t* __restrict__ perm, const int32_t* __restrict__ rp,
-                             const int32_t* __restrict__ ci, const double* __restrict__ vals,
+                             const int32_t* __restrict__ re, const int32_t* __restrict__ ci,
+                             const double* __restrict__ vals,
                              const int32_t* __restrict__ st, int32_t* __restrict__ col,
                              double* __restrict__ val, double* __restrict__ dinv, double* __restrict__ diag,
                              int lanes) {
@@ -482,7 +509,7 @@ __global__ void k_rel_gather(int32_t n, const int32_t* __restrict__ perm, const 
     const int64_t q = t >> lg;
     if (q >= n) return;
     const int32_t r = perm[q];
-    const int32_t a = rp[r], e = rp[r + 1] - 1, d = st[q];
+    const int32_t a = rp[r], e = re[r] - 1, d = st[q];
     if (col) {
 #pragma unroll 4
         for (int32_t k = a + li; k < e; k += lanes) col[d + (k - a)] = ci[k];
@@ -1132,7 +1159,8 @@ void fill_stats(ddf_plan_s* p, const std::vector<dcod>& hc) {
     S.depth = p->depth;
     S.levels = p->kind == DDF_SPTRSV ? p->nlevels : 0;
     S.blocks = p->nblocks;
-    S.nnz = p->nnz;
+    // SpTRSV: the entries of L (with lower_of_input, fewer than the input's)
+    S.nnz = p->kind == DDF_SPTRSV ? p->npts + p->n : p->nnz;
     S.points = p->npts;
     int64_t psc2_nof = 0, s_entries = 0;
     std::vector<int32_t> hst;
@@ -1160,10 +1188,20 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
     TRY(tmp.get(&err, 1));
     int32_t big = 0x7fffffff;
     DDF_CUDA_TRY(cudaMemcpyAsync(err, &big, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    // row ends of L: rowptr + 1, or (lower_of_input) the end of each row's
+    // lower part, computed after the general checks of the input
+    const bool lower = kind == DDF_SPTRSV && p->opts.lower_of_input;
+    const int32_t* rowend = rowptr + 1;
     const int gl = lanes_for_mean(p->nnz, n, VALIDATE_MAX_LANES);
     k_validate<<<ddf_grid(((int64_t)n + 1) * gl, TPB), TPB, 0, s>>>(n, p->n_cols, p->nnz, rowptr, colidx, values,
-                                                                   kind, err, gl);
+                                                                   lower ? (int)DDF_SPMV : kind, err, gl);
     ddf_count_launch();
+    if (lower && n > 0) {
+        TRY(ddf_alloc(&p->orig_rowend, n, s));
+        k_lower_end<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, p->nnz, rowptr, colidx, values, p->orig_rowend, err);
+        ddf_count_launch();
+        rowend = p->orig_rowend;
+    }
     DDF_CUDA_TRY(cudaGetLastError());
     int32_t herr = 0;
     TRY(d2h(&herr, err, 1, s));
@@ -1194,8 +1232,8 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
         DDF_CUDA_TRY(cudaMemsetAsync(maxlev, 0, sizeof(int32_t), s));
         DDF_CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(int32_t), s));
         if (n > 0) {
-            k_levels<<<ddf_grid(n, LEV_CHUNK), 32 * LEV_WARPS, 0, s>>>(n, rowptr, colidx, lev, tick, maxlev,
-                                                                       p->status, p->opts.spin_cap_ns);
+            k_levels<<<ddf_grid(n, LEV_CHUNK), 32 * LEV_WARPS, 0, s>>>(n, rowptr, rowend, colidx, lev, tick,
+                                                                       maxlev, p->status, p->opts.spin_cap_ns);
             ddf_count_launch();
         }
         DDF_CUDA_TRY(cudaGetLastError());
@@ -1251,12 +1289,13 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
         TRY(tmp.get(&lens, n));
         TRY(tmp.get(&st64, (int64_t)n + 1));
         if (n > 0) {
-            k_rel_lens<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, p->seq, rowptr, lens);
+            k_rel_lens<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, p->seq, rowptr, rowend, lens);
             ddf_count_launch();
         }
         TRY(ddf_scan_i32_to_i64(lens, st64, n, s));
-        // validated: every row holds exactly one diagonal entry, stored last
-        const int64_t npts = p->nnz - n;
+        // validated: every row of L holds exactly one diagonal entry, stored last
+        int64_t npts = p->nnz - n;
+        if (lower) TRY(d2h(&npts, st64 + n, 1, s));
         p->npts = npts;
         TRY(ddf_alloc(&p->starts, (int64_t)n + 1, s));
         k_i64_to_i32<<<ddf_grid(n + 1, TPB, 4096), TPB, 0, s>>>(st64, p->starts, (int64_t)n + 1);
@@ -1269,8 +1308,9 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
         if (p->opts.store_dtype != DDF_F64) TRY(ddf_alloc(&p->diag, n, s));
         if (n > 0) {
             const int gv = lanes_for_mean(npts, n, REL_GATHER_MAX_LANES);
-            k_rel_gather<<<ddf_grid((int64_t)n * gv, TPB), TPB, 0, s>>>(n, p->seq, rowptr, colidx, values, p->starts,
-                                                                        p->col, p->val, p->dinv, p->diag, gv);
+            k_rel_gather<<<ddf_grid((int64_t)n * gv, TPB), TPB, 0, s>>>(n, p->seq, rowptr, rowend, colidx, values,
+                                                                        p->starts, p->col, p->val, p->dinv, p->diag,
+                                                                        gv);
             ddf_count_launch();
         }
         DDF_CUDA_TRY(cudaGetLastError());
@@ -1495,7 +1535,8 @@ ddf_status ddf_gather_values(ddf_plan_s* p, const double* values, cudaStream_t s
     int32_t n = p->n;
     if (n > 0) {
         const int gv = lanes_for_mean(p->npts, n, REL_GATHER_MAX_LANES);
-        k_rel_gather<<<ddf_grid((int64_t)n * gv, TPB), TPB, 0, s>>>(n, p->seq, p->orig_rowptr, nullptr, values,
+        const int32_t* re = p->orig_rowend ? p->orig_rowend : p->orig_rowptr + 1;
+        k_rel_gather<<<ddf_grid((int64_t)n * gv, TPB), TPB, 0, s>>>(n, p->seq, p->orig_rowptr, re, nullptr, values,
                                                                    p->starts, nullptr, p->val, p->dinv, p->diag,
                                                                    gv);
         ddf_count_launch();

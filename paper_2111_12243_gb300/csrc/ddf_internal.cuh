@@ -71,7 +71,9 @@ struct ddf_plan_s {
     int32_t* seq;                 // SpTRSV: row at each position (level order); SpMV: NULL
     int32_t* part_ptr;            // [depth + 1]
     double* dinv;                 // SpTRSV: 1 / L_ii per position
-    int32_t* orig_rowptr;         // SpTRSV: rowptr of the inspected L (for ddf_update_values)
+    int32_t* orig_rowptr;         // SpTRSV: rowptr of the inspected matrix (for ddf_update_values)
+    int32_t* orig_rowend;         // SpTRSV with lower_of_input: end of each row's lower part
+                                  // (owned); NULL when the input is L itself (ends: orig_rowptr + 1)
     // codelets and units
     dcod* cod;
     int64_t ncod;

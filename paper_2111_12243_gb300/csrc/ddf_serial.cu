@@ -17,7 +17,7 @@
 namespace {
 
 constexpr char MAGIC[8] = {'D', 'D', 'F', 'P', 'L', 'A', 'N', '1'};
-constexpr int32_t VERSION = 3;
+constexpr int32_t VERSION = 4;
 
 struct Header {
     char magic[8];
@@ -67,6 +67,7 @@ std::vector<Piece> pieces(ddf_plan_s* p, const Header& h, void** slots[24]) {
         add((void**)&p->seq, 4 * (size_t)n);
         add((void**)&p->dinv, 8 * (size_t)n);
         add((void**)&p->orig_rowptr, 4 * (size_t)(n + 1));
+        if (h.opts.lower_of_input) add((void**)&p->orig_rowend, 4 * (size_t)n);
         if (h.nblocks > 0) {
             add((void**)&p->blk_ptr, 4 * (size_t)(h.nblocks + 1));
             add((void**)&p->esplit, 4 * (size_t)n);

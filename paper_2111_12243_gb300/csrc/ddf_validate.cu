@@ -135,6 +135,25 @@ __global__ void k_check_starts(int32_t n, int64_t npts, const int32_t* __restric
     if (q < n && st[q + 1] < st[q]) fail(err, DDF_ERR_OUT_OF_RANGE);
 }
 
+// SpTRSV: the inspected matrix's rows, kept for ddf_update_values, against
+// the plan's layout: position q holds row r = seq[q], whose entries
+// orig_rowptr[r] .. re[r] (re = orig_rowptr + 1, or orig_rowend) end with the
+// diagonal and fill starts[q] .. starts[q + 1] without it.
+__global__ void k_check_rows(int32_t n, int64_t nnz_in, const int32_t* __restrict__ seq,
+                             const int32_t* __restrict__ st, const int32_t* __restrict__ rp,
+                             const int32_t* __restrict__ re, int32_t* __restrict__ err) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int32_t r = seq[q];
+    if (r < 0 || r >= n) {
+        fail(err, DDF_ERR_OUT_OF_RANGE);
+        return;
+    }
+    const int32_t a = rp[r], e = re[r], b = rp[r + 1];
+    if (a < 0 || e <= a || e > b || (int64_t)b > nnz_in || (int64_t)e - a - 1 != (int64_t)st[q + 1] - st[q])
+        fail(err, DDF_ERR_OUT_OF_RANGE);
+}
+
 __device__ __forceinline__ bool lanes_ok(int32_t v) { return v >= 1 && v <= 32 && (v & (v - 1)) == 0; }
 
 // Coarsened SpTRSV plans: block and chunk tables, and every row of a block's
@@ -221,6 +240,11 @@ ddf_status ddf_plan_validate(ddf_plan_t p) {
         }
         if (n > 0) {
             k_check_starts<<<ddf_grid((int64_t)n + 1, 256), 256, 0, s>>>(n, npts, p->starts, err);
+            ddf_count_launch();
+        }
+        if (trsv && n > 0 && p->orig_rowptr) {
+            const int32_t* re = p->orig_rowend ? p->orig_rowend : p->orig_rowptr + 1;
+            k_check_rows<<<ddf_grid(n, 256), 256, 0, s>>>(n, p->nnz, p->seq, p->starts, p->orig_rowptr, re, err);
             ddf_count_launch();
         }
         if (trsv && n > 0 && p->nblocks > 0) {
