@@ -132,6 +132,21 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+class L2Flush:
+    """Between timed iterations: write a buffer larger than L2, then read
+    another one, so that the written lines are written back to DRAM here and
+    not during the timed work that follows (which then starts on a cold L2
+    holding clean lines only)."""
+
+    def __init__(self, torch, dev):
+        self.w = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+        self.r = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def __call__(self):
+        self.w.zero_()
+        self.r.sum()
+
+
 def aggregate(ms, exec_b, world, dev):
     """Whole-job figures over `world` replicas: the step time is the maximum
     over ranks, the value the bytes of all ranks over that time (GB/s)."""
@@ -167,7 +182,7 @@ def run_ours(args, rank, world, local_rank):
             "y": torch.empty(a.n_rows, dtype=torch.float64, device=dev),
             "xs": torch.empty(lo.n_rows, dtype=torch.float64, device=dev),
         })
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    flush = L2Flush(torch, dev)
     phases = ("inspect_spmv", "spmv", "inspect_sptrsv", "sptrsv")
 
     opts_L = ddf.ddf_opts_default(coarsen_rows=args.coarsen) if args.coarsen is not None else None
@@ -243,7 +258,7 @@ def run_ours(args, rank, world, local_rank):
         return evs, stats, se
 
     for _ in range(args.warmup):
-        flush.zero_()
+        flush()
         step(False)
     torch.cuda.synchronize()
     serial = None
@@ -254,13 +269,13 @@ def run_ours(args, rank, world, local_rank):
         step(False)
         sms = []
         for _ in range(args.steps):
-            flush.zero_()
+            flush()
             sms.append(step(False)[2])
         torch.cuda.synchronize()
         args.streams = keep
         serial = float(np.mean([a.elapsed_time(b) for a, b in sms]))
         for _ in range(args.warmup):
-            flush.zero_()
+            flush()
             step(False)
         torch.cuda.synchronize()
     launches0 = ddf.ddf_kernel_launches()
@@ -271,7 +286,7 @@ def run_ours(args, rank, world, local_rank):
     t0 = time.perf_counter()
     steps = []
     for _ in range(args.steps):
-        flush.zero_()
+        flush()
         steps.append(step(False))
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
@@ -438,7 +453,7 @@ def run_batch(args, ddf, torch, dev, stream, flush, nrhs=32, reps=5):
     def timed(fn, r=reps):
         ts = []
         for _ in range(r):
-            flush.zero_()
+            flush()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             fn()
@@ -506,7 +521,7 @@ def run_mixed(D, ddf, torch, stream, flush, breakdown, reps=5):
     def timed(fn):
         ts = []
         for _ in range(reps):
-            flush.zero_()
+            flush()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             fn()
@@ -758,7 +773,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": "+".join(WORKLOAD), "scale": args.scale,
                        "step": "inspect(A)+spmv+inspect(L)+sptrsv per matrix",
-                       "l2": "256 MB flush between steps; inputs larger than L2",
+                       "l2": "256 MB written then another 256 MB read between steps (the flush's "
+                             "write-back happens before the timed work); inputs larger than L2",
                        "streams": {1: "everything on one stream",
                                    2: "one stream and host thread per matrix",
                                    4: "one stream and host thread per chain: inspect(A)+spmv, "
