@@ -287,7 +287,9 @@ DDF_API ddf_status ddf_plan_load(const void* buf, size_t len, ddf_stream_t s, dd
  * Check every index an executor derives from the plan against the arrays it
  * addresses (Sec. III's access functions: for each codelet the rows f(i0),
  * the value extents g(i0, i1) and the columns h(i0, i1); the work units; the
- * level pointers; the coarsened block and chunk tables), and for SpTRSV that
+ * level pointers; the coarsened block and chunk tables; for SpTRSV the rows
+ * of the inspected matrix kept for ddf_update_values, each of which must
+ * fill exactly its position's extent), and for SpTRSV that
  * every column names a row below the diagonal that an earlier partition
  * (Algorithm 1's level or block schedule) solves.  Returns DDF_OK,
  * DDF_ERR_ARG (a malformed descriptor, unit or table), DDF_ERR_OUT_OF_RANGE
