@@ -1,13 +1,23 @@
 #!/usr/bin/env python
 """Benchmark of the DDF hot path on one GB300 (or N independent replicas).
 
-One step = the whole path over the workload "lap7_128+elast3x3_64" (a 3-D
-7-point Laplacian on a 128^3 grid and a 3x3-block elasticity matrix on a 27-point
-stencil over 64^3 nodes): for each matrix A and its lower triangle L,
-    ddf_inspect(A, SpMV) -> ddf_spmv -> ddf_inspect(L, SpTRSV) -> ddf_sptrsv
+One step = the whole path over the headline workload (default "st27_168": a
+3-D 27-point stencil on a 168^3 grid, 4.74M rows, 126.5M nonzeros, the
+largest single-GPU configuration): for each matrix A and its lower triangle L,
+    ddf_inspect(A, SpMV) -> ddf_spmv      ddf_inspect(L, SpTRSV) -> ddf_sptrsv
 with CSR inputs and vectors already resident in HBM.  ``value`` is the
 executors' algorithmic bytes (plan statistics) moved per second of the whole
-step, inspection included.  Extra keys report each phase on its own.
+step, inspection included.  Extra keys report:
+  exec_only        the executors alone with their plans reused (Sec. V-C amortisation)
+  roofline         the dominant executor call of the step against the measured HBM copy bandwidth
+  roofline_spmv    the SpMV alone, with its FP64-pipe ceiling
+  critical_path    the SpTRSV bound max(bytes / bandwidth, depth x t_hop)
+  extra            other workloads (default the power-law matrix), each phase alone
+  mixed_precision  FP32 / BF16 SpMV and refined SpTRSV on the 27-point stencil, integer
+                   and N(0,1) values, errors against the CPU oracle
+  ablation_e5      plans restricted to BLAS + PSC II codelets against all types (Sec. V)
+  blas_banded      a band matrix, whose plan is BLAS codelets
+  batched          256 uneven matrices x 32 right-hand sides in one CUDA graph
 
 ``--impl reference`` times the CPU oracle (plain sequential C, FP64) on the
 host cores over the same workload and prints the same line with
@@ -17,12 +27,12 @@ from __future__ import annotations
 
 import argparse
 import json
-import threading
 import os
 import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 import numpy as np
@@ -33,23 +43,37 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "SpMV & SpTRSV GB/s as % of HBM roofline; mixed-precision vs FP64 speedup"
-WORKLOAD = ("lap7_128", "elast3x3_64")
+DEFAULT_WORKLOAD = "st27_168"
+DEFAULT_EXTRA = "powerlaw_4m"
+DEFAULT_MIXED = "st27_168+st27r_168"
+DEFAULT_ABLATION = "st27_168+lap7_128"
 L2_FLUSH_BYTES = 256 << 20
 FALLBACK_HBM_GBS = 6800.0
+# FP64 fused multiply-adds one GB300 SM issues per clock (1.25 TFLOP/s nominal
+# FP64 over 152 SMs at 2.07 GHz): one per stored value of an FP64 SpMV, which
+# caps it below the HBM bandwidth
+FP64_FMA_PER_SM_CLK = 2
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    help="matrices of the timed step, joined by '+' (names of synth.WORKLOADS)")
+    ap.add_argument("--extra", default=DEFAULT_EXTRA, help="workloads timed phase by phase ('' = none)")
+    ap.add_argument("--mixed", default=DEFAULT_MIXED, help="workloads of the mixed-precision section")
+    ap.add_argument("--ablation", default=DEFAULT_ABLATION, help="workloads of the E5 ablation")
     ap.add_argument("--scale", type=float, default=1.0, help="grid scale (1.0 = the full workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-ablation", action="store_true")
+    ap.add_argument("--no-banded", action="store_true")
     ap.add_argument("--no-critical-path", action="store_true", help="skip the chain solve that measures t_hop")
     ap.add_argument("--streams", type=int, default=4, choices=[1, 2, 4],
                     help="1: everything on one stream; 2: one stream and host thread per matrix; "
@@ -58,10 +82,14 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--coarsen", type=int, default=None,
                     help="SpTRSV rows per block (coarsen_rows; 0 = plain level sets; default: library default)")
-    a = ap.parse_args()
+    a = ap.parse_args(argv)
     if a.serial:
         a.streams = 1
     return a
+
+
+def names(spec):
+    return [s for s in (spec or "").split("+") if s]
 
 
 def peaks():
@@ -73,9 +101,9 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def build_inputs(scale):
+def build_inputs(workload, scale):
     mats = []
-    for name in WORKLOAD:
+    for name in names(workload):
         a, lo, x, b = synth.workload(name, scale)
         mats.append((name, a, lo, x, b))
     return mats
@@ -93,12 +121,12 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, interval_ms=100):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.p = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", str(interval_ms)],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -123,8 +151,8 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        names_ = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names_[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
 
@@ -158,6 +186,73 @@ def aggregate(ms, exec_b, world, dev):
     return ms, exec_b * world / (ms * 1e-3) / 1e9
 
 
+def make_timer(torch, stream, flush):
+    def timed(fn, reps=5):
+        """Median device time (ms) of fn over `reps` calls, L2 flushed before each."""
+        ts = []
+        for _ in range(reps):
+            flush()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+    return timed
+
+
+def sptrsv_flops(st):
+    # Sec. V: SpTRSV = 2 (nnz_L - n) + n divisions
+    return 2 * (st["nnz"] - st["n_rows"]) + st["n_rows"]
+
+
+def solo(ddf, torch, dev, timed, a, lo, x, b, opts_a=None, opts_l=None, do_sptrsv=True):
+    """Each phase of one matrix alone on the GPU: inspection of A and L, then
+    the SpMV and the SpTRSV with their plans reused.  Median of 5, L2 flushed."""
+    td = lambda v: torch.from_numpy(np.ascontiguousarray(v)).to(dev)  # noqa: E731
+    A = (td(a.rowptr), td(a.colidx), td(a.values))
+    xd = td(x)
+    y = torch.empty(a.n_rows, dtype=torch.float64, device=dev)
+    out = {"n": a.n_rows, "nnz": a.nnz}
+    holder = {}
+
+    def insp_a():
+        if "pA" in holder:
+            holder.pop("pA").destroy()
+        holder["pA"] = ddf.ddf_inspect(*A, a.n_cols, ddf.DDF_SPMV, opts_a)
+    out["inspect_spmv_ms"] = round(timed(insp_a), 4)
+    pA = holder.pop("pA")
+    sa = ddf.ddf_plan_stats(pA)
+    t = timed(lambda: ddf.ddf_spmv(pA, xd, y))
+    out.update({"spmv_ms": round(t, 4), "spmv_bytes": sa["bytes_exec"],
+                "spmv_gbs": round(sa["bytes_exec"] / (t * 1e-3) / 1e9, 1),
+                "spmv_gflops": round(2 * sa["nnz"] / (t * 1e-3) / 1e9, 1),
+                "codelets_spmv": sa["ncodelets"], "ops_spmv": sa["ops"], "units_spmv": sa["nunits"]})
+    pA.destroy()
+    del A
+    if do_sptrsv:
+        L = (td(lo.rowptr), td(lo.colidx), td(lo.values))
+        bd = td(b)
+        xs = torch.empty(lo.n_rows, dtype=torch.float64, device=dev)
+
+        def insp_l():
+            if "pL" in holder:
+                holder.pop("pL").destroy()
+            holder["pL"] = ddf.ddf_inspect(*L, lo.n_cols, ddf.DDF_SPTRSV, opts_l)
+        out["inspect_sptrsv_ms"] = round(timed(insp_l), 4)
+        pL = holder.pop("pL")
+        sl = ddf.ddf_plan_stats(pL)
+        t = timed(lambda: ddf.ddf_sptrsv(pL, bd, xs))
+        out.update({"sptrsv_ms": round(t, 4), "sptrsv_bytes": sl["bytes_exec"],
+                    "sptrsv_gbs": round(sl["bytes_exec"] / (t * 1e-3) / 1e9, 1),
+                    "sptrsv_gflops": round(sptrsv_flops(sl) / (t * 1e-3) / 1e9, 1),
+                    "sptrsv_status": ddf.ddf_get_status(pL), "depth": sl["levels"],
+                    "codelets_sptrsv": sl["ncodelets"], "ops_sptrsv": sl["ops"]})
+        pL.destroy()
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2111_12243_gb300 as ddf
@@ -167,7 +262,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
-    mats = build_inputs(args.scale)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mats = build_inputs(args.workload, args.scale)
 
     def to_dev(a):
         return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -175,7 +271,7 @@ def run_ours(args, rank, world, local_rank):
     D = []
     for name, a, lo, x, b in mats:
         D.append({
-            "name": name, "a": a, "lo": lo,
+            "name": name, "a": a, "lo": lo, "xh": x, "bh": b,
             "A": (to_dev(a.rowptr), to_dev(a.colidx), to_dev(a.values)),
             "L": (to_dev(lo.rowptr), to_dev(lo.colidx), to_dev(lo.values)),
             "x": to_dev(x), "b": to_dev(b),
@@ -183,6 +279,7 @@ def run_ours(args, rank, world, local_rank):
             "xs": torch.empty(lo.n_rows, dtype=torch.float64, device=dev),
         })
     flush = L2Flush(torch, dev)
+    timed = make_timer(torch, stream, flush)
     phases = ("inspect_spmv", "spmv", "inspect_sptrsv", "sptrsv")
 
     opts_L = ddf.ddf_opts_default(coarsen_rows=args.coarsen) if args.coarsen is not None else None
@@ -240,9 +337,8 @@ def run_ours(args, rank, world, local_rank):
             used = side if args.streams == 2 else side + side_l
             for s in used:
                 s.wait_stream(stream)
-            # host threads start one after another, each some 0.1-0.7 ms after
-            # the last: the longest chains go first (the L chains, larger matrix
-            # first, then the A chains)
+            # host threads start one after another: the longest chains go
+            # first (the L chains, larger matrix first, then the A chains)
             if args.streams == 2:
                 jobs = [(one, i, side[i]) for i in order]
             else:
@@ -257,6 +353,9 @@ def run_ours(args, rank, world, local_rank):
         se[1].record(stream)
         return evs, stats, se
 
+    # clocks are sampled from the first warm-up step until the executors have
+    # also been timed alone (a window of seconds, the timed steps inside it)
+    clocks = ClockSampler(local_rank)
     for _ in range(args.warmup):
         flush()
         step(False)
@@ -282,7 +381,6 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local_rank)
     t0 = time.perf_counter()
     steps = []
     for _ in range(args.steps):
@@ -292,7 +390,6 @@ def run_ours(args, rank, world, local_rank):
     wall = time.perf_counter() - t0
     if world > 1:
         torch.distributed.barrier()
-    clk = clocks.stop()
     launches = ddf.ddf_kernel_launches() - launches0
 
     # per-phase times (ms) and bytes
@@ -335,7 +432,8 @@ def run_ours(args, rank, world, local_rank):
             "sptrsv_bytes": sl["bytes_exec"],
             # FLOPs (Sec. V): SpMV 2 nnz; SpTRSV 2 (nnz_L - n) + n divisions
             "spmv_gflops": round(2 * sa["nnz"] / (t_spmv * 1e-3) / 1e9, 1),
-            "sptrsv_gflops": round((2 * (sl["nnz"] - sl["n_rows"]) + sl["n_rows"]) / (t_trsv * 1e-3) / 1e9, 1),
+            "sptrsv_gflops": round(sptrsv_flops(sl) / (t_trsv * 1e-3) / 1e9, 1),
+            "nnz": sa["nnz"], "nnz_lower": sl["nnz"],
             "depth": sl["levels"],
             "partitions": sl["depth"],
             "blocks": sl["blocks"],
@@ -350,47 +448,96 @@ def run_ours(args, rank, world, local_rank):
     t_dom, dom, dom_bytes = max(cand)
     achieved = dom_bytes / (t_dom * 1e-3) / 1e9
     # DRAM bytes per launch: the ratio (dram read + write) / algorithmic bytes
-    # from one ncu capture of the half-scale case, applied to this launch's
-    # algorithmic bytes (the traffic scales with the rows processed).
+    # from one ncu capture of a smaller case of the same kernel, applied to
+    # this launch's algorithmic bytes (the traffic scales with the rows).
     ratio = TRAFFIC_RATIO.get(dom)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
                 "unit": "GB/s", "frac": round(achieved / hbm, 4),
                 "traffic": round(ratio * dom_bytes) if ratio else None,
-                "peak_source": f"{peak_kind} copy bandwidth"}
+                "peak_source": f"{peak_kind} copy bandwidth",
+                "timed": "CUDA events around the call on its stream, inside the timed steps"}
 
-    critical = None if args.no_critical_path else critical_path(ddf, torch, dev, stream, breakdown, hbm)
+    # the executors alone, their plans reused (the amortised case of Sec. V-C)
+    exec_only = {}
+    for d in D:
+        exec_only[d["name"]] = solo(ddf, torch, dev, timed, d["a"], d["lo"], d["xh"], d["bh"], None, opts_L)
+    clk = clocks.stop()
+    clk["window"] = "warm-up steps, timed steps and the executors alone"
+    # SpMV of the first matrix: roofline against HBM and its FP64-pipe ceiling
+    e0 = exec_only[D[0]["name"]]
+    f_clk = (clk.get("sm_mhz") or 2070.0) * 1e6
+    ceil = e0["spmv_bytes"] * FP64_FMA_PER_SM_CLK * n_sm * f_clk / e0["nnz"] / 1e9
+    roofline_spmv = {"bound": "hbm", "kernel": f"ddf_spmv[{D[0]['name']}]", "achieved": e0["spmv_gbs"],
+                     "peak": hbm, "unit": "GB/s", "frac": round(e0["spmv_gbs"] / hbm, 4),
+                     "traffic": round(TRAFFIC_RATIO[f"ddf_spmv[{D[0]['name']}]"] * e0["spmv_bytes"])
+                     if f"ddf_spmv[{D[0]['name']}]" in TRAFFIC_RATIO else None,
+                     "fp64_fma_ceiling_gbs": round(ceil, 1),
+                     "frac_of_fp64_ceiling": round(e0["spmv_gbs"] / ceil, 4),
+                     "fp64_ceiling": f"{FP64_FMA_PER_SM_CLK} FP64 FMA per SM per clock x {n_sm} SMs x "
+                                     f"{f_clk / 1e6:.0f} MHz, one FMA per nonzero, "
+                                     f"{e0['spmv_bytes'] / e0['nnz']:.2f} algorithmic bytes per nonzero",
+                     "timed": "alone, median of 5, L2 flushed"}
+
+    t_hop = None if args.no_critical_path else chain_hop(ddf, torch, dev, stream)
+    critical = None if t_hop is None else critical_path(t_hop, breakdown, exec_only, hbm)
 
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, D, ddf, torch, dev, stream, exec_b, world)
+    host = {d["name"]: (d["a"], d["lo"], d["xh"], d["bh"]) for d in D}
+    del D
+    torch.cuda.empty_cache()
+    extra = None
+    if names(args.extra):
+        extra = {}
+        for nm in names(args.extra):
+            a, lo, x, b = synth.workload(nm, args.scale)
+            r = solo(ddf, torch, dev, timed, a, lo, x, b, None, opts_L)
+            if t_hop is not None:
+                t_bw = r["sptrsv_bytes"] / (hbm * 1e9) * 1e6
+                t_lat = r["depth"] * t_hop
+                r["critical_path"] = {"levels": r["depth"], "bytes_bound_us": round(t_bw, 1),
+                                      "depth_x_hop_us": round(t_lat, 1),
+                                      "bound": "latency" if t_lat >= t_bw else "hbm",
+                                      "measured_us": round(r["sptrsv_ms"] * 1e3, 1),
+                                      "us_per_level": round(r["sptrsv_ms"] * 1e3 / max(r["depth"], 1), 3),
+                                      "frac_of_bound": round(max(t_bw, t_lat) / (r["sptrsv_ms"] * 1e3), 3)}
+            r["spmv_frac_of_hbm"] = round(r["spmv_gbs"] / hbm, 4)
+            extra[nm] = r
+            del a, lo
     mixed = None
-    if not args.no_mixed:
-        mixed = run_mixed(D, ddf, torch, stream, flush, breakdown)
+    if not args.no_mixed and names(args.mixed):
+        mixed = run_mixed(args, host, ddf, torch, dev, timed)
+    ablation = None
+    if not args.no_ablation and names(args.ablation):
+        ablation = run_ablation(args, host, ddf, torch, dev, timed)
+    banded = None
+    if not args.no_banded:
+        banded = run_banded(args, ddf, torch, dev, timed, hbm)
     batched = None
     if not args.no_batch:
-        del D
         torch.cuda.empty_cache()
         batched = run_batch(args, ddf, torch, dev, stream, flush)
 
     return {
         "value": value, "ms_per_step": ms, "wall_s": wall, "launches": launches, "clocks": clk,
-        "breakdown": breakdown, "roofline": roofline, "critical_path": critical, "e2e": e2e,
+        "breakdown": breakdown, "roofline": roofline, "roofline_spmv": roofline_spmv,
+        "critical_path": critical, "e2e": e2e, "exec_only": exec_only,
         "serial_ms_per_step": serial, "timeline": timeline,
-        "exec_bytes_per_step": exec_b,
-        "mixed": mixed, "batched": batched,
+        "exec_bytes_per_step": exec_b, "extra": extra,
+        "mixed": mixed, "ablation": ablation, "banded": banded, "batched": batched,
     }
 
 
 # (dram__bytes_read.sum + dram__bytes_write.sum) / algorithmic bytes of one
-# launch, from one ncu capture of the half-scale workload (elasticity 32^3
-# nodes: 38.59 MB of DRAM traffic for 36.34 MB of algorithmic bytes).
-TRAFFIC_RATIO = {"ddf_sptrsv[elast3x3_64]": (38545152 + 47104) / 36341468}
+# launch, from one ncu capture of a smaller case of the same kernel (the
+# captures are summarised under profiles/).
+TRAFFIC_RATIO = {}
 
 
-def critical_path(ddf, torch, dev, stream, breakdown, hbm, n_chain=8192, reps=5):
-    """The SpTRSV bound max(bytes / HBM bandwidth, depth x t_hop).  t_hop, the
-    cost of one dependency level, is measured on a pure chain (a bidiagonal
-    matrix: n levels of one row each) with the same executor."""
+def chain_hop(ddf, torch, dev, stream, n_chain=8192, reps=5):
+    """t_hop, the cost of one dependency level (us), measured on a pure chain
+    (a bidiagonal matrix: n levels of one row each) with the same executor."""
     ch = synth.chain(n_chain)
     td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
     q = ddf.ddf_inspect(td(ch.rowptr), td(ch.colidx), td(ch.values), ch.n_cols, ddf.DDF_SPTRSV)
@@ -405,18 +552,26 @@ def critical_path(ddf, torch, dev, stream, breakdown, hbm, n_chain=8192, reps=5)
         torch.cuda.synchronize()
         if i:
             ts.append(e0.elapsed_time(e1))
-    if ddf.ddf_get_status(q, stream=stream) != 0:
-        return None
-    t_hop = float(np.median(ts)) * 1e3 / n_chain           # us per level
+    ok = ddf.ddf_get_status(q, stream=stream) == 0
+    q.destroy()
+    return float(np.median(ts)) * 1e3 / n_chain if ok else None
+
+
+def critical_path(t_hop, breakdown, exec_only, hbm, n_chain=8192):
+    """The SpTRSV bound max(bytes / HBM bandwidth, depth x t_hop), against the
+    solve inside the step and alone."""
     out = {"t_hop_us": round(t_hop, 3), "chain_rows": n_chain}
     for nm, bd in breakdown.items():
         t_bw = bd["sptrsv_bytes"] / (hbm * 1e9) * 1e6           # us at the measured copy bandwidth
         t_lat = bd["depth"] * t_hop
         bound = max(t_bw, t_lat)
         meas = bd["sptrsv_ms"] * 1e3
+        alone = exec_only[nm]["sptrsv_ms"] * 1e3
         out[nm] = {"levels": bd["depth"], "bytes_bound_us": round(t_bw, 1), "depth_x_hop_us": round(t_lat, 1),
                    "bound": "latency" if t_lat >= t_bw else "hbm", "measured_us": round(meas, 1),
-                   "frac_of_bound": round(bound / meas, 3)}
+                   "frac_of_bound": round(bound / meas, 3), "alone_us": round(alone, 1),
+                   "alone_us_per_level": round(alone / max(bd["depth"], 1), 3),
+                   "alone_frac_of_bound": round(bound / alone, 3)}
     return out
 
 
@@ -449,21 +604,12 @@ def run_batch(args, ddf, torch, dev, stream, flush, nrhs=32, reps=5):
             ddf.ddf_spmm(pA, X, Y, nrhs, stream=side)
             ddf.ddf_sptrsm(pL, X, Xs, nrhs, stream=side)
     stream.wait_stream(side)
+    timed = make_timer(torch, stream, flush)
 
-    def timed(fn, r=reps):
-        ts = []
-        for _ in range(r):
-            flush()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        return float(np.median(ts))
-
-    t_graph = timed(g.replay)
+    t_graph = timed(g.replay, reps)
     st_graph = ddf.ddf_get_status(pL)
+    t_spmm = timed(lambda: ddf.ddf_spmm(pA, X, Y, nrhs), reps)
+    t_trsm = timed(lambda: ddf.ddf_sptrsm(pL, X, Xs, nrhs), reps)
     sa, sl = ddf.ddf_plan_stats(pA), ddf.ddf_plan_stats(pL)
     nnzA, nnzL = sa["points"], sl["points"]
     # algorithmic bytes: FP32 values once, the 32-wide blocks read once and written once
@@ -497,6 +643,8 @@ def run_batch(args, ddf, torch, dev, stream, flush, nrhs=32, reps=5):
                 ddf.ddf_sptrsv(pl64[i], X64[k, a:b], S64[k, a:b])
 
     t_plain = timed(plain, 1)
+    g.replay()
+    torch.cuda.synchronize()
     err = float(torch.linalg.norm(Y.double().t() - Y64) / torch.linalg.norm(Y64))
     errs = float(torch.linalg.norm(Xs.double().t() - S64) / torch.linalg.norm(S64))
     for p in pa + pl + pa64 + pl64 + [pA, pL]:
@@ -505,79 +653,120 @@ def run_batch(args, ddf, torch, dev, stream, flush, nrhs=32, reps=5):
             "dtype": "f32 values and vectors, f32 sums", "tile_spmm_unit_nnz": tile_spmv,
             "tile_sptrsm_units_per_cta": tile_trsv, "graph_ms": round(t_graph, 4), "graph_status": st_graph,
             "graph_gbs": round((bytes_spmm + bytes_trsm) / (t_graph * 1e-3) / 1e9, 1),
+            "spmm_ms": round(t_spmm, 4), "spmm_gbs": round(bytes_spmm / (t_spmm * 1e-3) / 1e9, 1),
+            "sptrsm_ms": round(t_trsm, 4), "sptrsm_gbs": round(bytes_trsm / (t_trsm * 1e-3) / 1e9, 1),
             "per_matrix_multi_rhs_ms": round(t_per, 3), "speedup_vs_per_matrix": round(t_per / t_graph, 2),
             "plain_fp64_per_rhs_ms": round(t_plain, 2), "speedup_vs_plain_fp64": round(t_plain / t_graph, 2),
             "spmm_relerr_vs_fp64": err, "sptrsm_relerr_vs_fp64": errs}
 
 
-def run_mixed(D, ddf, torch, stream, flush, breakdown, reps=5):
-    """FP32 / BF16 executors against the FP64 ones on the same matrices: SpMV
-    with low-precision values and vectors (FP32 sums), SpTRSV as low-precision
-    solves refined in FP64 to a relative residual of 1e-12.  Errors are stated
-    against the FP64 executor's result (itself within 1e-12 of the FP64 CPU
-    oracle in the parity tests)."""
+def relerr(a, b):
+    nb = float(np.linalg.norm(b))
+    return float(np.linalg.norm(np.asarray(a, dtype=np.float64) - b) / nb) if nb > 0 else float(
+        np.linalg.norm(np.asarray(a, dtype=np.float64) - b))
+
+
+def run_mixed(args, host, ddf, torch, dev, timed):
+    """The precision form: FP32 / BF16 executors against the FP64 ones on the
+    same matrices.  SpMV with low-precision values and vectors (FP32 sums);
+    SpTRSV as low-precision solves refined in FP64 to a relative residual of
+    1e-12.  Errors are stated against the CPU oracle's FP64 results, which the
+    CPU-baseline leg computes (oracle_references); without that leg they are
+    stated against the GPU FP64 executors."""
+    refs = None if args.no_cpu_baseline else oracle_references(args, host)
     out = {}
-
-    def timed(fn):
-        ts = []
-        for _ in range(reps):
-            flush()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        return float(np.median(ts))
-
-    for d in D:
-        nm = d["name"]
-        a, lo = d["a"], d["lo"]
-        res = {}
-        p64 = ddf.ddf_inspect(*d["A"], a.n_cols, ddf.DDF_SPMV)
-        ddf.ddf_spmv(p64, d["x"], d["y"])
-        y64 = d["y"].clone()
-        t64 = timed(lambda: ddf.ddf_spmv(p64, d["x"], d["y"]))
+    td = lambda v: torch.from_numpy(np.ascontiguousarray(v)).to(dev)  # noqa: E731
+    for nm in names(args.mixed):
+        a, lo, x, b = host[nm] if nm in host else synth.workload(nm, args.scale)
+        A = (td(a.rowptr), td(a.colidx), td(a.values))
+        L = (td(lo.rowptr), td(lo.colidx), td(lo.values))
+        xd, bd = td(x), td(b)
+        y = torch.empty(a.n_rows, dtype=torch.float64, device=dev)
+        xs = torch.empty(lo.n_rows, dtype=torch.float64, device=dev)
+        res = {"values": "integer 26 / -1" if nm.startswith("st27_") else "N(0,1), diagonal 1 + sum |row|"}
+        p64 = ddf.ddf_inspect(*A, a.n_cols, ddf.DDF_SPMV)
+        t64 = timed(lambda: ddf.ddf_spmv(p64, xd, y))
+        y64 = y.cpu().numpy()
         st64 = ddf.ddf_plan_stats(p64)
+        p64.destroy()
+        ref_y = refs[nm]["y"] if refs else y64
+        res["against"] = "cpu oracle (fp64)" if refs else "gpu fp64 executor"
         res["spmv_f64_ms"] = round(t64, 4)
+        res["spmv_f64_gbs"] = round(st64["bytes_exec"] / (t64 * 1e-3) / 1e9, 1)
+        res["spmv_f64_relerr"] = relerr(y64, ref_y)
         for dt, tdt, name, vs in ((ddf.DDF_F32, torch.float32, "f32", 4), (ddf.DDF_BF16, torch.bfloat16, "bf16", 2)):
-            pl = ddf.ddf_inspect(*d["A"], a.n_cols, ddf.DDF_SPMV, ddf.ddf_opts_default(store_dtype=dt))
-            xl = d["x"].to(tdt)
-            yl = torch.empty(a.n_rows, dtype=tdt, device=d["x"].device)
+            pl = ddf.ddf_inspect(*A, a.n_cols, ddf.DDF_SPMV, ddf.ddf_opts_default(store_dtype=dt))
+            xl = xd.to(tdt)
+            yl = torch.empty(a.n_rows, dtype=tdt, device=dev)
             t = timed(lambda: ddf.ddf_spmv_lowp(pl, xl, yl))
-            err = float(torch.linalg.norm(yl.double() - y64) / torch.linalg.norm(y64))
             lp_bytes = st64["bytes_exec"] - (8 - vs) * (st64["points"] + a.n_cols + a.n_rows)
             res[f"spmv_{name}_ms"] = round(t, 4)
             res[f"spmv_{name}_speedup"] = round(t64 / t, 3)
             res[f"spmv_{name}_gbs"] = round(lp_bytes / (t * 1e-3) / 1e9, 1)
-            res[f"spmv_{name}_relerr"] = err
+            res[f"spmv_{name}_relerr"] = relerr(yl.double().cpu().numpy(), ref_y)
             pl.destroy()
-        p64.destroy()
-        q64 = ddf.ddf_inspect(*d["L"], lo.n_cols, ddf.DDF_SPTRSV)
-        ddf.ddf_sptrsv(q64, d["b"], d["xs"])
-        x64 = d["xs"].clone()
-        tq = timed(lambda: ddf.ddf_sptrsv(q64, d["b"], d["xs"]))
-        res["sptrsv_f64_ms"] = round(tq, 4)
+        del A
+        q64 = ddf.ddf_inspect(*L, lo.n_cols, ddf.DDF_SPTRSV)
+        tq = timed(lambda: ddf.ddf_sptrsv(q64, bd, xs))
+        x64 = xs.cpu().numpy()
+        res["sptrsv_f64_status"] = ddf.ddf_get_status(q64)
         q64.destroy()
+        ref_x = refs[nm]["x"] if refs else x64
+        res["sptrsv_f64_ms"] = round(tq, 4)
+        res["sptrsv_f64_relerr"] = relerr(x64, ref_x)
         for dt, name in ((ddf.DDF_F32, "f32"), (ddf.DDF_BF16, "bf16")):
-            ql = ddf.ddf_inspect(*d["L"], lo.n_cols, ddf.DDF_SPTRSV, ddf.ddf_opts_default(store_dtype=dt))
-            xr = torch.empty(lo.n_rows, dtype=torch.float64, device=d["x"].device)
+            ql = ddf.ddf_inspect(*L, lo.n_cols, ddf.DDF_SPTRSV, ddf.ddf_opts_default(store_dtype=dt))
+            xr = torch.empty(lo.n_rows, dtype=torch.float64, device=dev)
             info = {}
 
             def go():
-                info["r"] = ddf.ddf_sptrsv_refine(ql, d["b"], xr, tol=1e-12, max_iter=30)
+                info["r"] = ddf.ddf_sptrsv_refine(ql, bd, xr, tol=1e-12, max_iter=30)
 
             t = timed(go)
             st, iters, rel = info["r"]
+            xh = xr.cpu().numpy()
             res[f"sptrsv_refine_{name}_ms"] = round(t, 4)
             res[f"sptrsv_refine_{name}_speedup"] = round(tq / t, 3)
             res[f"sptrsv_refine_{name}_iters"] = iters
-            res[f"sptrsv_refine_{name}_relres"] = rel
+            res[f"sptrsv_refine_{name}_relres_gpu"] = rel
             res[f"sptrsv_refine_{name}_status"] = st
-            res[f"sptrsv_refine_{name}_relerr"] = float(torch.linalg.norm(xr - x64) / torch.linalg.norm(x64))
+            res[f"sptrsv_refine_{name}_relerr"] = relerr(xh, ref_x)
+            if refs:
+                res[f"sptrsv_refine_{name}_relres_oracle"] = oracle_relres(lo, xh, b)
             ql.destroy()
+        del L
         out[nm] = res
     return out
+
+
+def run_ablation(args, host, ddf, torch, dev, timed):
+    """E5 (Sec. V, the BLAS-only comparison): plans restricted to BLAS codelets
+    (plus PSC II, which covers whatever BLAS does not) against plans with every
+    codelet type, executors timed alone."""
+    out = {}
+    for nm in names(args.ablation):
+        a, lo, x, b = host[nm] if nm in host else synth.workload(nm, args.scale)
+        full = solo(ddf, torch, dev, timed, a, lo, x, b)
+        ob = ddf.ddf_opts_default(allowed_types=ddf.DDF_ALLOW_BLAS | ddf.DDF_ALLOW_PSC2)
+        bl = solo(ddf, torch, dev, timed, a, lo, x, b, ob, ob)
+        out[nm] = {"all_types": {k: full[k] for k in ("spmv_ms", "spmv_gbs", "sptrsv_ms", "sptrsv_gbs",
+                                                     "codelets_spmv", "ops_spmv", "codelets_sptrsv")},
+                   "blas_psc2": {k: bl[k] for k in ("spmv_ms", "spmv_gbs", "sptrsv_ms", "sptrsv_gbs",
+                                                   "codelets_spmv", "ops_spmv", "codelets_sptrsv")},
+                   "spmv_speedup_all_vs_blas": round(bl["spmv_ms"] / full["spmv_ms"], 3),
+                   "sptrsv_speedup_all_vs_blas": round(bl["sptrsv_ms"] / full["sptrsv_ms"], 3)}
+    return out
+
+
+def run_banded(args, ddf, torch, dev, timed, hbm, n=1 << 22, half_bw=8):
+    """A band matrix of 17 nonzeros per row: its plan is BLAS codelets, so this
+    times the BLAS SpMV kernel where it dominates."""
+    m = synth.banded(max(1024, int(n * args.scale)), half_bw)
+    x = synth.uniform_vector(m.n_cols, synth.SEED_BASE + 7)
+    r = solo(ddf, torch, dev, timed, m, None, x, None, do_sptrsv=False)
+    r["matrix"] = f"band, half bandwidth {half_bw}, N(0,1), diagonal 1 + sum |row|"
+    r["spmv_frac_of_hbm"] = round(r["spmv_gbs"] / hbm, 4)
+    return r
 
 
 def run_e2e(args, D, ddf, torch, dev, stream, exec_b, world):
@@ -589,19 +778,18 @@ def run_e2e(args, D, ddf, torch, dev, stream, exec_b, world):
         pin = lambda v: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()  # noqa: E731
         H.append({"A": (pin(a.rowptr), pin(a.colidx), pin(a.values)),
                   "L": (pin(lo.rowptr), pin(lo.colidx), pin(lo.values)),
-                  "x": pin(d["x"].cpu().numpy()), "b": pin(d["b"].cpu().numpy()),
+                  "x": pin(d["xh"]), "b": pin(d["bh"]),
                   "y": torch.empty(a.n_rows, dtype=torch.float64).pin_memory(),
                   "xs": torch.empty(lo.n_rows, dtype=torch.float64).pin_memory()})
         h2d += csr_bytes(a) + csr_bytes(lo) + 8 * a.n_cols + 8 * lo.n_rows
         d2h += 8 * a.n_rows + 8 * lo.n_rows
 
-    # The four chains (inspect(A) + spmv and inspect(L) + sptrsv of each
-    # matrix) run on their own streams and host threads, as in the
-    # device-resident step.  Uploads go on one copy stream, longest chain
-    # first (the L chains, larger matrix first, then the A chains), and each
-    # chain's stream waits only for its own arrays: the long solve chains
-    # start while the remaining arrays are still being copied, instead of
-    # after all of them.
+    # The chains (inspect(A) + spmv and inspect(L) + sptrsv of each matrix)
+    # run on their own streams and host threads, as in the device-resident
+    # step.  Uploads go on one copy stream, longest chain first (the L chains,
+    # larger matrix first, then the A chains), and each chain's stream waits
+    # only for its own arrays: the long solve chains start while the remaining
+    # arrays are still being copied, instead of after all of them.
     opts_L = ddf.ddf_opts_default(coarsen_rows=args.coarsen) if args.coarsen is not None else None
     copy = torch.cuda.Stream(device=dev)
     size = lambda i: D[i]["a"].nnz + D[i]["lo"].nnz  # noqa: E731
@@ -725,15 +913,55 @@ def run_oracle(mats, seconds, max_steps=None, warmup=0):
     return times
 
 
-def main():
-    args = parse()
+def oracle_spmv_cores(mats, reps=5):
+    """The SpMV of the workload on the host: the sequential oracle (one core,
+    the paper's baseline definition) and the row-parallel oracle over every
+    host core; median of `reps`, GB/s of the executor's CSR bytes."""
+    import oracle
+    cores = os.cpu_count() or 1
+    out = {"cores": cores}
+    for key, fn in (("sequential", lambda a, x: oracle.spmv(a, x)),
+                    ("parallel", lambda a, x: oracle.spmv_par(a, x, cores))):
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            for name, a, lo, x, b in mats:
+                fn(a, x)
+            ts.append(time.perf_counter() - t0)
+        t = float(np.median(ts))
+        byts = sum(12 * a.nnz + 4 * (a.n_rows + 1) + 8 * (a.n_cols + a.n_rows) for _, a, _, _, _ in mats)
+        out[key] = {"ms": round(t * 1e3, 2), "gbs": round(byts / t / 1e9, 3)}
+    return out
+
+
+def oracle_references(args, host):
+    """The CPU oracle's FP64 results for the mixed-precision matrices (part of
+    the CPU-baseline leg): y = A x and the forward substitution of L x = b."""
+    import oracle
+    oracle.build()
+    refs = {}
+    for nm in names(args.mixed):
+        a, lo, x, b = host[nm] if nm in host else synth.workload(nm, args.scale)
+        refs[nm] = {"y": oracle.spmv_par(a, x), "x": oracle.sptrsv(lo, b)}
+    return refs
+
+
+def oracle_relres(lo, x, b):
+    """||b - L x||_2 / ||b||_2 with the oracle's FP64 product."""
+    import oracle
+    r = b - oracle.spmv_par(lo, x)
+    return float(np.linalg.norm(r) / np.linalg.norm(b))
+
+
+def main(argv=None):
+    args = parse(argv)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         if rank != 0:
             return 0
-        mats = build_inputs(args.scale)
+        mats = build_inputs(args.workload, args.scale)
         times = run_oracle(mats, 0, max_steps=args.steps, warmup=args.warmup)
         b = oracle_exec_bytes(mats)
         ms = 1e3 * float(np.mean(times))
@@ -742,7 +970,7 @@ def main():
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(ms, 2), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": "+".join(WORKLOAD), "scale": args.scale},
+                "config": {"workload": args.workload, "scale": args.scale},
                 "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                                  "sample": "the full workload per step, sequential C oracle"},
                 "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
@@ -757,13 +985,14 @@ def main():
     r = run_ours(args, rank, world, local_rank)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        mats = build_inputs(args.scale)
+        mats = build_inputs(args.workload, args.scale)
         times = run_oracle(mats, args.cpu_seconds)
         b = oracle_exec_bytes(mats)
         cv = b / float(np.mean(times)) / 1e9
         cpu = {"value": round(cv, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"{len(times)} full steps of the workload (sequential C oracle, "
-                         f"{sum(times):.1f} s)", "exec_bytes_oracle_plan": b}
+                         f"{sum(times):.1f} s)", "exec_bytes_oracle_plan": b,
+               "spmv_host_cores": oracle_spmv_cores(mats)}
     if rank == 0:
         hbm, _ = peaks()
         line = {
@@ -771,7 +1000,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r["ms_per_step"], 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "+".join(WORKLOAD), "scale": args.scale,
+            "config": {"workload": args.workload, "scale": args.scale,
                        "step": "inspect(A)+spmv+inspect(L)+sptrsv per matrix",
                        "l2": "256 MB written then another 256 MB read between steps (the flush's "
                              "write-back happens before the timed work); inputs larger than L2",
@@ -782,7 +1011,9 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single"},
             "frac_of_hbm": round(r["value"] / hbm, 4),
             "roofline": r["roofline"],
+            "roofline_spmv": r["roofline_spmv"],
             "critical_path": r["critical_path"],
+            "exec_only": r["exec_only"],
             "serial": None if r["serial_ms_per_step"] is None else {
                 "ms_per_step": round(r["serial_ms_per_step"], 4),
                 "value": round(r["exec_bytes_per_step"] / (r["serial_ms_per_step"] * 1e-3) / 1e9, 2)},
@@ -794,7 +1025,10 @@ def main():
             # [start, end] of each chain (A: inspect(A) + spmv, L: inspect(L) +
             # sptrsv) in ms after the step's start event, mean over the timed steps
             "timeline_ms": r["timeline"],
+            "extra": r["extra"],
             "mixed_precision": r["mixed"],
+            "ablation_e5": r["ablation"],
+            "blas_banded": r["banded"],
             "batched": r["batched"],
             "exec_bytes_per_step": r["exec_bytes_per_step"],
         }

@@ -128,7 +128,7 @@ typedef struct {
     int64_t nnz;                          /* stored entries of the inspected matrix          */
     int64_t points;                       /* iteration points (SpTRSV: off-diagonal entries) */
     int64_t ncodelets[3];
-    int64_t ops[3];                       /* iteration points covered by each type (Fig. 8)  */
+    int64_t ops[3];                       /* iteration points covered by each type (Fig. 9)  */
     int64_t rows[3];                      /* rows covered by each type                        */
     int64_t nunits;                       /* executor work units                              */
     int64_t bytes_exec;                   /* algorithmic bytes of one execute call            */
@@ -159,30 +159,50 @@ DDF_API ddf_status ddf_inspect(const ddf_csr* A, ddf_kind kind, const ddf_opts* 
                        ddf_plan_t* out);
 
 /* Replace the plan's values with a new array of the same pattern (nnz entries
- * in the original CSR order), without re-inspection.  values is a device
- * pointer when on_device != 0.  SpTRSV: fails with DDF_ERR_ZERO_DIAG when a
- * new diagonal entry is 0 (synchronises s in that case only to report it). */
+ * in the original CSR order), without re-inspection.  The inspector reads only
+ * the pattern and the executor the values (Listing 2: DDF_Inspector is given
+ * A.pattern(), the vectorised kernel A itself), so one inspection serves every
+ * matrix of that pattern, the amortisation of its cost in Sec. V-C.  values is
+ * a device pointer when on_device != 0; it is read during the call and may be
+ * freed afterwards.  The plan stores the values in its executor layout (level
+ * order for SpTRSV; for SpMV, CSR order except rows executed in value tiles,
+ * whose values are point-major).  SpTRSV: fails with DDF_ERR_ZERO_DIAG when a
+ * new diagonal entry is 0 (synchronises s in that case only to report it);
+ * DDF_ERR_ARG for a NULL plan or values, DDF_ERR_OOM / DDF_ERR_CUDA when a
+ * staging copy of host values cannot be made. */
 DDF_API ddf_status ddf_update_values(ddf_plan_t p, const double* values, int32_t on_device,
                              ddf_stream_t s);
 
-/* SpMV executor: y = A x.  x [n_cols] and y [n_rows] are device pointers;
- * y is overwritten (rows without entries get 0).  Launches one kernel per
- * codelet type present (BLAS, PSC I, PSC II) on s. */
+/* SpMV executor (Sec. IV-B, the executor of Listing 3): y = A x with
+ * y_i = sum_k A_ik x_k as the CSR code of Fig. 1a computes it, each codelet of
+ * the plan run by the generic code of its type (Sec. III-B: BLAS, PSC I,
+ * PSC II).  x [n_cols] and y [n_rows] are FP64 device pointers, caller-owned;
+ * y is overwritten (rows without entries get 0) and must not overlap x.
+ * Launches one kernel per codelet type and layout present on s (BLAS and
+ * PSC I rows of at most 256 points run one lane per row; the rest
+ * in warp work units) and returns without synchronising.  Returns
+ * DDF_ERR_WRONG_KIND for a SpTRSV plan, DDF_ERR_ARG for NULL vectors or a plan
+ * without values. */
 DDF_API ddf_status ddf_spmv(ddf_plan_t p, const double* x, double* y, ddf_stream_t s);
 
-/* SpTRSV executor: solves L x = b by forward substitution.  b and x are
- * device pointers of n_rows entries and must not overlap.  Rows are run
- * level by level, codelets of one level together, levels linked by per-row
- * ready flags (x itself: an entry is ready once it no longer holds the fill
- * pattern written at the start of the call).  Every dependency wait is
- * bounded by spin_cap_ns; a wait that runs out latches DDF_ERR_TIMEOUT in the
- * plan's status word (read it with ddf_get_status) and the solve finishes
- * with NaN in the affected rows instead of hanging. */
+/* SpTRSV executor (Sec. IV-B over the partitions of Sec. IV-A): solves
+ * L x = b by forward substitution, x_i = (b_i - sum_{j<i} L_ij x_j) / L_ii.
+ * b and x are FP64 device pointers of n_rows entries, caller-owned, and must
+ * not overlap.  The partitions of findDependencies / partitionIterationSpace
+ * (level sets of the dependency graph G, or their coarsened form) run in
+ * order and the codelets of one partition together, linked by per-row ready
+ * flags instead of a barrier (x itself: an entry is ready once it no longer
+ * holds the fill pattern written at the start of the call).  Asynchronous on
+ * s.  Every dependency wait is bounded by spin_cap_ns; a wait that runs out
+ * latches DDF_ERR_TIMEOUT in the plan's status word (read it with
+ * ddf_get_status) and the solve finishes with NaN in the affected rows
+ * instead of hanging.  Returns DDF_ERR_WRONG_KIND for a SpMV plan and
+ * DDF_ERR_ARG for NULL or overlapping vectors. */
 DDF_API ddf_status ddf_sptrsv(ddf_plan_t p, const double* b, double* x, ddf_stream_t s);
 
 /*
- * Mixed-precision SpMV (a later form of the executor, beyond the paper's FP64
- * codelets): the plan must have been inspected with store_dtype DDF_F32 or
+ * Mixed-precision SpMV (a later form of the executor of Sec. IV-B; the paper
+ * runs its codelets in double precision, Listing 3): the plan must have been inspected with store_dtype DDF_F32 or
  * DDF_BF16.  y = A x with the values in that type, x and y device vectors of
  * vec_dtype (DDF_F32 or DDF_BF16), every product and sum in FP32.  Same
  * codelets and kernels per type as ddf_spmv.
@@ -245,21 +265,31 @@ DDF_API ddf_status ddf_sptrsm(ddf_plan_t p, const void* B, void* X, int32_t nrhs
 DDF_API ddf_status ddf_tune(ddf_plan_t p, const void* in, void* out, int32_t nrhs, ddf_dtype dtype,
                             ddf_stream_t s, int32_t* best_unit_nnz);
 
-/* Synchronise s, then return and clear the plan's device status word. */
+/* Synchronise s, then return and clear the plan's device status word: the
+ * errors only the executor can see while it runs the partitions of Sec. IV-A
+ * in order (DDF_ERR_TIMEOUT: a dependency wait ran out).  DDF_OK when none
+ * occurred; DDF_ERR_CUDA when the stream itself reported an error. */
 DDF_API ddf_status ddf_get_status(ddf_plan_t p, ddf_stream_t s);
 
-/* Plan statistics (host struct).  Synchronous. */
+/* Plan statistics (host struct st, caller-owned): counts of codelets, rows
+ * and operations per type (the breakdown of Fig. 9 in Sec. V-A), the number
+ * of partitions and of levels of G (Sec. IV-A), and the executor's
+ * algorithmic bytes per call.  Synchronous (computed on the first call from a
+ * host copy of the descriptors).  DDF_ERR_ARG for NULL arguments. */
 DDF_API ddf_status ddf_plan_stats(ddf_plan_t p, ddf_plan_stats_t* st);
 
 /*
- * Export the plan in canonical form for checking:
+ * Export the plan in canonical form for checking: the codelet list cList of
+ * Alg. 1 with, for each codelet, the access functions of Sec. III-A (f: row,
+ * g: value offset, h: column) in the strided form of Sec. III-D, and the
+ * partitions of Sec. IV-A.  Buffers are host memory owned by the caller:
  *   records [ncodelets][12] int64: part, type, q0, m, n, f_str, rho, g_str,
  *            gamma, h0, delta, sigma (n = -1 for PSC II; rho, gamma, delta,
  *            sigma are 0 where undefined, e.g. for one-row codelets);
  *   seq [n_rows] int32: the partition sequence (row at each position);
  *   part_ptr [depth + 1] int32: first position of each partition;
- *   gs [n_rows] int64: offset of each position's first value in the plan's
- *            value layout (CSR order for SpMV, level order for SpTRSV).
+ *   gs [n_rows] int64: g(q, 0), the offset of each position's first value in
+ *            CSR order for SpMV and in the level-ordered copy for SpTRSV.
  * Any output pointer may be NULL to skip it; *ncodelets and *depth always
  * receive the sizes.  Synchronous.
  */
@@ -350,13 +380,18 @@ DDF_API ddf_status ddf_debug_fail_alloc(int64_t k);
  * that every GPU which loads the library holds until the process exits.
  * n > DDF_NOALLOC_MAX_ROWS returns DDF_ERR_TOO_LARGE before any device work.
  *
- * The first call on a device looks up the device address of that array
- * (cudaGetSymbolAddress, with the device current); make that first call
- * before any stream capture.  Every call shares the array: its header is
- * cleared at the start of each call, and rows are flagged with a per-call
- * number, so stale flags of earlier calls are never mistaken for new ones;
- * calls that overlap on the GPU (two streams, two threads) race and must not
- * be issued.  The call synchronises stream s and returns the solve's status:
+ * Every call looks up the device address of that array in the current
+ * context (cudaGetSymbolAddress, with the device current; the lookup itself
+ * allocates nothing).  The very first lookup in a context loads the library's
+ * module, and loading the module is what creates the array: a caller that
+ * must not allocate later makes one call with n == 0 first, as a warm-up (it
+ * does the look-up and returns DDF_OK without touching the GPU otherwise).
+ * Every call shares the array: its header is cleared at the start of each
+ * call, and rows are flagged with a per-call number, so stale flags of
+ * earlier calls are never mistaken for new ones; calls that overlap on the
+ * GPU (two streams, two threads) race and must not be issued.  The call
+ * copies the status to the host and synchronises stream s, so it cannot be
+ * recorded in a CUDA graph.  It returns the solve's status:
  * DDF_ERR_MISSING_DIAG / DDF_ERR_NOT_LOWER / DDF_ERR_ZERO_DIAG for a
  * malformed row (detected on the device; such rows are skipped, never read
  * out of bounds), DDF_ERR_TIMEOUT when a dependency wait exceeds

@@ -8,6 +8,8 @@
  * Contents (paper: "Vectorizing Sparse Matrix Codes with Dependency Driven
  * Trace Analysis", Cetinic, Cheshmi, Dehnavi):
  *   ora_spmv_csr        y = A x in CSR order            (Fig. 1a; Sec. V baseline)
+ *   ora_spmv_csr_par    the same rows split over host threads (each row
+ *                       still summed in CSR order, so y is bit-identical)
  *   ora_sptrsv_csr      forward substitution L x = b     (Sec. V baseline)
  *   ora_levels          longest-path levels of G         (Sec. IV-A, findDependencies)
  *   ora_level_order     rows ordered by (level, row)     (Sec. IV-A, partitionIterationSpace)
@@ -52,6 +54,7 @@
  *       PSC II codelet.  min_cost keeps the cheapest; ties prefer BLAS_first,
  *       then PSCI_first.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -78,6 +81,72 @@ int ora_spmv_csr(int32_t n, const int32_t* Ap, const int32_t* Ai, const double* 
         for (int32_t k = Ap[i]; k < Ap[i + 1]; ++k) s += Ax[k] * x[Ai[k]];
         y[i] = s;
     }
+    return ORA_OK;
+}
+
+/* Row-parallel SpMV: thread t takes the rows whose entries start in the t-th
+ * of T equal shares of the nonzeros, and computes each of them exactly as
+ * ora_spmv_csr does.  The multi-core CPU baseline; y equals the sequential
+ * result bit for bit. */
+typedef struct {
+    int32_t r0, r1;
+    const int32_t *Ap, *Ai;
+    const double *Ax, *x;
+    double* y;
+} spmv_job;
+
+static void* spmv_rows(void* arg) {
+    const spmv_job* j = (const spmv_job*)arg;
+    for (int32_t i = j->r0; i < j->r1; ++i) {
+        double s = 0.0;
+        for (int32_t k = j->Ap[i]; k < j->Ap[i + 1]; ++k) s += j->Ax[k] * j->x[j->Ai[k]];
+        j->y[i] = s;
+    }
+    return NULL;
+}
+
+/* first row i in [0, n] with Ap[i] >= target */
+static int32_t first_row_at(int32_t n, const int32_t* Ap, int64_t target) {
+    int32_t lo = 0, hi = n;
+    while (lo < hi) {
+        int32_t mid = lo + (hi - lo) / 2;
+        if ((int64_t)Ap[mid] < target) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+int ora_spmv_csr_par(int32_t n, const int32_t* Ap, const int32_t* Ai, const double* Ax,
+                     const double* x, double* y, int32_t nthreads) {
+    if (nthreads < 1 || nthreads > 1024) return ORA_ERR_ARG;
+    spmv_job* jobs = (spmv_job*)malloc(sizeof(spmv_job) * (size_t)nthreads);
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    if (!jobs || !th) {
+        free(jobs);
+        free(th);
+        return ORA_ERR_OOM;
+    }
+    const int64_t nnz = n > 0 ? Ap[n] : 0;
+    for (int32_t t = 0; t < nthreads; ++t) {
+        jobs[t].r0 = t == 0 ? 0 : first_row_at(n, Ap, nnz * t / nthreads);
+        jobs[t].r1 = t == nthreads - 1 ? n : first_row_at(n, Ap, nnz * (t + 1) / nthreads);
+        jobs[t].Ap = Ap;
+        jobs[t].Ai = Ai;
+        jobs[t].Ax = Ax;
+        jobs[t].x = x;
+        jobs[t].y = y;
+    }
+    int32_t started = 0;
+    for (int32_t t = 1; t < nthreads; ++t) {
+        if (pthread_create(&th[t], NULL, spmv_rows, &jobs[t]) != 0) break;
+        started = t;
+    }
+    spmv_rows(&jobs[0]);
+    /* threads that could not be started run here, in order */
+    for (int32_t t = started + 1; t < nthreads; ++t) spmv_rows(&jobs[t]);
+    for (int32_t t = 1; t <= started; ++t) pthread_join(th[t], NULL);
+    free(jobs);
+    free(th);
     return ORA_OK;
 }
 

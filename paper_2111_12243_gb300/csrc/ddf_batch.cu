@@ -56,17 +56,19 @@ __device__ __forceinline__ int32_t point_col(const dcod& C, const int32_t* __res
 }
 
 // y_r[k] = sum over the row's points of a * x_col[k], k = lane < nrhs.
+// Point i1's value is val[kb + i1 * vs] (vs > 1 for rows of SpMV value tiles).
 template <typename TV, typename TX>
 __device__ __forceinline__ TX row_mrhs(const dcod& C, int32_t i0, const int32_t* __restrict__ st,
                                       const int32_t* __restrict__ col, const TV* __restrict__ val,
-                                      const TX* __restrict__ X, int32_t nrhs, int lane) {
+                                      const TX* __restrict__ X, int32_t nrhs, int lane, int32_t vs = 1,
+                                      int32_t vb = -1) {
     const int32_t q = C.q0 + i0;
     int32_t kb, L;
     if (C.type == DDF_PSC2) {
         kb = st[q];
         L = st[q + 1] - kb;
     } else {
-        kb = C.g0 + C.gamma * i0;
+        kb = vb >= 0 ? vb : C.g0 + C.gamma * i0;
         L = C.n;
     }
     TX acc = 0;
@@ -75,7 +77,7 @@ __device__ __forceinline__ TX row_mrhs(const dcod& C, int32_t i0, const int32_t*
         TX pv = 0;
         int32_t pj = 0;
         if (i1 < L) {
-            pv = ddf_cvt<TX>(__ldcs(val + kb + i1));
+            pv = ddf_cvt<TX>(__ldcs(val + kb + (int64_t)i1 * vs));
             pj = point_col(C, col, i0, kb, i1);
         }
         const int32_t cnt = min(32, L - p0);
@@ -108,6 +110,26 @@ k_spmm(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64_t nu
                 const TX acc = row_mrhs<TV, TX>(C, i0, st, col, val, X, nrhs, lane);
                 if (lane < nrhs) Y[(int64_t)(C.f0 + C.rho * i0) * nrhs + lane] = acc;
             }
+        }
+    }
+}
+
+// Rows of SpMV value tiles (point-major values), one warp per tile.
+template <typename TV, typename TX>
+__global__ void __launch_bounds__(DDF_CTA_THREADS)
+k_spmm_tile(const dcod* __restrict__ cod, const dtile* __restrict__ tiles, int64_t ntiles,
+            const int32_t* __restrict__ st, const int32_t* __restrict__ col, const TV* __restrict__ val,
+            const TX* __restrict__ X, TX* __restrict__ Y, int32_t nrhs) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles; t += nw) {
+        const dtile T = tiles[t];
+        const int32_t w = (int32_t)(T.meta & 7u) + 1;
+        for (int32_t r = 0; r < w; ++r) {
+            const dcod C = cod[T.cod + (int32_t)((T.meta >> (3 + 3 * r)) & 7u)];
+            const int32_t i0 = T.q + r - C.q0;
+            const TX acc = row_mrhs<TV, TX>(C, i0, st, col, val, X, nrhs, lane, w, T.vb + r);
+            if (lane < nrhs) Y[(int64_t)(C.f0 + C.rho * i0) * nrhs + lane] = acc;
         }
     }
 }
@@ -244,6 +266,13 @@ ddf_status launch_spmm(ddf_plan_s* p, const TV* val, const TX* X, TX* Y, int32_t
         if (p->nunits[t] <= 0) continue;
         k_spmm<TV, TX><<<grid_units(p->nunits[t], sm), DDF_CTA_THREADS, 0, s>>>(
             p->cod, p->units[t], p->nunits[t], p->starts, p->col, val, X, Y, nrhs);
+        ddf_count_launch();
+        ++launches;
+    }
+    for (int t = 0; t < 2; ++t) {
+        if (p->ntiles[t] <= 0) continue;
+        k_spmm_tile<TV, TX><<<grid_units(p->ntiles[t], sm), DDF_CTA_THREADS, 0, s>>>(
+            p->cod, p->tiles[t], p->ntiles[t], p->starts, p->col, val, X, Y, nrhs);
         ddf_count_launch();
         ++launches;
     }

@@ -55,6 +55,8 @@ void release(ddf_plan_s* p) {
     ddf_free(p->orig_rowend, s);
     ddf_free(p->cod, s);
     for (int k = 0; k < 3; ++k) ddf_free(p->units[k], s);
+    for (int k = 0; k < 2; ++k) ddf_free(p->tiles[k], s);
+    ddf_free(p->unit_q, s);
     ddf_free(p->status, s);
     ddf_free(p->ticket, s);
     if (p->val_lp) (void)cudaFreeAsync(p->val_lp, s);
@@ -153,30 +155,25 @@ ddf_status ddf_finish_plan(ddf_plan_s* p, int32_t* rp, int32_t* ci, double* v, c
                            bool borrowed) {
     const ddf_kind kind = p->kind;
     ddf_status st = DDF_OK;
-    if (kind == DDF_SPMV && p->nnz > 0 && v == nullptr) {
-        // values come later through ddf_update_values: reserve them now
-        st = ddf_alloc(&v, p->nnz, s);
-        if (!st) {
-            st = ddf_build_plan(p, rp, ci, nullptr, s);
-            if (!st) {
-                p->val = v;
-                v = nullptr;
-            }
-        }
-    } else {
-        st = ddf_build_plan(p, rp, ci, v, s);
-    }
     if (kind == DDF_SPMV) {
-        // on success the plan adopted rp / ci / v as its own arrays
+        // The pattern is inspected first; the plan's own value array is then
+        // filled from v in the executor's layout (tiles point-major).  Without
+        // values it is reserved for ddf_update_values.
+        st = ddf_build_plan(p, rp, ci, nullptr, s);
+        p->val = nullptr;
+        if (!st) st = ddf_alloc(&p->val, p->nnz, s);
+        if (!st && v != nullptr) st = ddf_gather_values(p, v, s);
+        // on success the plan adopted rp / ci as its own arrays; v is released
+        // unless it is borrowed (the caller's device values)
         if (st) {
             p->starts = nullptr;
             p->col = nullptr;
-            p->val = nullptr;
             ddf_free(rp, s);
             ddf_free(ci, s);
-            ddf_free(v, s);
         }
+        if (!borrowed) ddf_free(v, s);
     } else {
+        st = ddf_build_plan(p, rp, ci, v, s);
         // SpTRSV keeps rowptr (as orig_rowptr) and drops the CSR copies
         if (p->orig_rowptr != rp) ddf_free(rp, s);
         if (!borrowed) {
@@ -261,11 +258,16 @@ ddf_status ddf_inspect(const ddf_csr* A, ddf_kind kind, const ddf_opts* o, ddf_s
     double* v = nullptr;
     // A SpTRSV plan keeps only rowptr of the input (its columns and values are
     // re-laid in level order), so device-resident columns and values are read
-    // in place during inspection instead of being copied first.
-    const bool borrow = A->on_device && kind == DDF_SPTRSV;
+    // in place during inspection instead of being copied first.  A SpMV plan
+    // keeps copies of rowptr and the columns; its values are written once, in
+    // the executor's layout, from the caller's device array.
+    const bool borrow = A->on_device && (kind == DDF_SPTRSV || kind == DDF_SPMV);
     st = stage(&rp, A->rowptr, (int64_t)A->n_rows + 1, A->on_device, s);
-    if (borrow) {
+    if (borrow && kind == DDF_SPTRSV) {
         ci = const_cast<int32_t*>(A->colidx);
+        v = const_cast<double*>(A->values);
+    } else if (borrow) {
+        if (!st) st = stage(&ci, A->colidx, A->nnz, A->on_device, s);
         v = const_cast<double*>(A->values);
     } else {
         if (!st) st = stage(&ci, A->colidx, A->nnz, A->on_device, s);
@@ -273,10 +275,8 @@ ddf_status ddf_inspect(const ddf_csr* A, ddf_kind kind, const ddf_opts* o, ddf_s
     }
     if (st) {
         ddf_free(rp, s);
-        if (!borrow) {
-            ddf_free(ci, s);
-            ddf_free(v, s);
-        }
+        if (!borrow || kind == DDF_SPMV) ddf_free(ci, s);
+        if (!borrow) ddf_free(v, s);
         ddf_plan_destroy(p);
         return st;
     }

@@ -12,6 +12,8 @@
 #define DDF_WARPS_PER_CTA 8
 #define DDF_CTA_THREADS (32 * DDF_WARPS_PER_CTA)
 #define DDF_SOLVE_CTAS_PER_SM 2   // resident CTAs per SM of the level-set solve (measured: 1 and 4 are slower)
+#define DDF_SOLVE_PTS 2           // points per lane the level-set solve holds in registers: a solve
+                                  // unit gives a row of L points ceil(L / DDF_SOLVE_PTS) lanes
 // Coarsened solve: a partition is cut into chunks of at most DDF_BLK_ROWS_CAP
 // rows and DDF_BLK_ENT_CAP points, the unit staged into shared memory; a row
 // longer than DDF_BLK_ENT_CAP is a chunk of its own, run from global memory.
@@ -45,7 +47,28 @@ struct dcod {
 };
 static_assert(sizeof(dcod) == 64, "dcod layout");
 
-enum { DC_F_STRIDED = 1, DC_G_STRIDED = 2 };
+enum { DC_F_STRIDED = 1, DC_G_STRIDED = 2, DC_TILED = 4 };
+
+// SpMV value tiles.  Consecutive BLAS / PSC I codelets of one type and one
+// row length n <= DDF_TILE_NMAX whose rows follow each other form a run
+// (dcod.pad0 = first position of the run, pad1 = one past its last; flag
+// DC_TILED).  A run is cut into tiles of DDF_TILE_ROWS consecutive rows from
+// its first position, and each tile's w x n values (the same range of the
+// plan's value array that the rows occupy in CSR order) are stored point-major:
+// point i1 of row r of the tile at tile base + i1 * w + r.  The executor then
+// runs one lane per row, and the lanes of a tile read one contiguous stretch
+// per point.
+#define DDF_TILE_ROWS 8
+#define DDF_TILE_NMAX 256
+
+// One tile of the SpMV executor: rows q .. q + w - 1, values from vb (the
+// tile's first row's CSR offset); row q + r belongs to codelet
+// cod + ((meta >> (3 + 3 r)) & 7), and w = (meta & 7) + 1.
+struct dtile {
+    int32_t q, cod, vb;
+    uint32_t meta;
+};
+static_assert(sizeof(dtile) == 16, "dtile layout");
 
 // Executor work unit: rows [i0b, i0e) of codelet `cod`, processed by one warp
 // with `v` lanes per row (a power of two, 1..32).
@@ -78,8 +101,12 @@ struct ddf_plan_s {
     dcod* cod;
     int64_t ncod;
     int64_t ncod_type[3];
-    dunit* units[3];              // SpMV: one list per type; SpTRSV: units[0] = all, level order
+    dunit* units[3];              // SpMV: one list per type (codelets not in tiles); SpTRSV:
+                                  // units[0] = all, level order
     int64_t nunits[3];
+    int32_t* unit_q;              // SpTRSV: first position of each unit of units[0]
+    dtile* tiles[2];              // SpMV: tiles of tiled BLAS / PSC I codelets (DC_TILED)
+    int64_t ntiles[2];
     // device scratch / status
     int32_t* status;              // device status word (ddf_status)
     uint32_t* ticket;             // SpTRSV: work ticket
@@ -95,7 +122,7 @@ struct ddf_plan_s {
     double* r64;                  // residual b - L x (row order)
     float* rlp;                   // residual rounded to FP32 (right-hand side of a correction)
     float* xlp;                   // low-precision solution / correction
-    double* nrm;                  // two FP64 accumulators (||b||^2, ||r||^2)
+    double* nrm;                  // ||b||^2, ||r||^2 (FP64 accumulators) and a copy of the status word
     // coarsened SpTRSV plans (opts.coarsen_rows = R > 0): partitions are the
     // (block of R rows, level) pairs; part_ptr then has depth + 1 entries with
     // depth = number of partitions, and nlevels is the depth of G
@@ -187,6 +214,8 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
 ddf_status ddf_gather_values(ddf_plan_s* p, const double* values, cudaStream_t s);
 ddf_status ddf_compute_stats(ddf_plan_s* p);
 ddf_status ddf_build_units(ddf_plan_s* p, cudaStream_t s);
+ddf_status ddf_mark_tiles(ddf_plan_s* p, cudaStream_t s);
+ddf_status ddf_build_unit_q(ddf_plan_s* p, cudaStream_t s);
 // ddf_capi.cu
 ddf_status ddf_new_plan(ddf_kind kind, const ddf_opts* o, cudaStream_t s, int32_t n, int32_t n_cols, int64_t nnz,
                         ddf_plan_s** out);

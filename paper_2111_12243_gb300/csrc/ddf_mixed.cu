@@ -11,6 +11,7 @@
 // dependency chain of the level sets again: the method trades bytes per solve
 // for more solves.
 #include <math.h>
+#include <string.h>
 
 #include "ddf_internal.cuh"
 
@@ -55,23 +56,58 @@ __global__ void k_rhs(const double* __restrict__ b, float* __restrict__ blp, int
 
 // r = b - L x in FP64 over the level-ordered copy: position q holds row
 // seq[q], its off-diagonal entries starts[q] .. starts[q+1] and L_qq = diag[q].
-// Also ||r||^2 and r rounded to FP32.
+// Also ||r||^2 and r rounded to FP32.  A thread sums a row of up to
+// RES_LONG off-diagonal entries by itself (one FP64 multiply-add per entry,
+// no reduction); longer rows (the power-law matrix has rows of thousands of
+// entries) are collected by a ballot and summed by the whole warp, lanes
+// striding over the entries.  The sum of squares goes to nrm[1]; thread 0
+// also copies the plan's status word into nrm[2], so that one copy returns
+// the norms and the solve's status.
+constexpr int32_t RES_LONG = 64;
+
 __global__ void k_residual(int32_t n, const int32_t* __restrict__ seq, const int32_t* __restrict__ st,
                            const int32_t* __restrict__ col, const double* __restrict__ val,
                            const double* __restrict__ diag, const double* __restrict__ b,
                            const double* __restrict__ x, double* __restrict__ r, float* __restrict__ rlp,
-                           double* __restrict__ nrm) {
+                           double* __restrict__ nrm, const int32_t* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) reinterpret_cast<int32_t*>(nrm + 2)[0] = *status;
     double s2 = 0.0;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t row = seq[q];
-        double acc = diag[q] * x[row];
-        for (int32_t k = st[q]; k < st[q + 1]; ++k) acc += val[k] * x[col[k]];
-        const double rv = b[row] - acc;
-        r[row] = rv;
-        rlp[row] = (float)rv;
-        s2 += rv * rv;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // the loop runs the same number of times on every lane of a warp
+    const int64_t q_end = ((int64_t)n + 31) / 32 * 32;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < q_end; q += stride) {
+        const bool in = q < n;
+        int32_t a = 0, e = 0, row = 0;
+        if (in) {
+            row = seq[q];
+            a = st[q];
+            e = st[q + 1];
+        }
+        const bool lng = in && e - a > RES_LONG;
+        double acc = 0.0;
+        if (in && !lng) {
+            acc = diag[q] * x[row];
+            for (int32_t k = a; k < e; ++k) acc += val[k] * x[col[k]];
+        }
+        // long rows: the warp sums each in turn
+        for (unsigned m = __ballot_sync(0xffffffffu, lng); m; m &= m - 1) {
+            const int src = __ffs(m) - 1;
+            const int32_t la = __shfl_sync(0xffffffffu, a, src), le = __shfl_sync(0xffffffffu, e, src);
+            double part = 0.0;
+            for (int32_t k = la + lane; k < le; k += 32) part += val[k] * x[col[k]];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            if (lane == src) acc = diag[q] * x[row] + part;
+        }
+        if (in) {
+            const double rv = b[row] - acc;
+            r[row] = rv;
+            rlp[row] = (float)rv;
+            s2 += rv * rv;
+        }
     }
-    block_add(s2, nrm);
+    block_add(s2, nrm + 1);
 }
 
 // x = d (first step) or x += d, FP64 update of an FP32 correction
@@ -102,7 +138,7 @@ ddf_status ddf_make_lowp(ddf_plan_s* p, cudaStream_t s) {
         if (!st && !p->r64) st = ddf_alloc(&p->r64, p->n, s);
         if (!st && !p->rlp) st = ddf_alloc(&p->rlp, p->n, s);
         if (!st && !p->xlp) st = ddf_alloc(&p->xlp, p->n, s);
-        if (!st && !p->nrm) st = ddf_alloc(&p->nrm, 2, s);
+        if (!st && !p->nrm) st = ddf_alloc(&p->nrm, 3, s);   // ||b||^2, ||r||^2, status word
         if (st) return st;
     }
     if (!p->has_values) return DDF_OK;
@@ -136,19 +172,20 @@ ddf_status ddf_refine(ddf_plan_s* p, const double* b, double* x, double tol, int
     k_update<<<gs(n, sm), 256, 0, s>>>(x, p->xlp, n, 1);
     ddf_count_launch();
     ++launches;
-    double h[2] = {0.0, 0.0};
+    double h[3] = {0.0, 0.0, 0.0};
     double nb = 0.0, rel = 0.0;
     int32_t it = 0;
     for (;; ++it) {
         DDF_CUDA_TRY(cudaMemsetAsync(p->nrm + 1, 0, sizeof(double), s));
         k_residual<<<gs(n, sm), 256, 0, s>>>((int32_t)n, p->seq, p->starts, p->col, p->val, p->diag, b, x, p->r64,
-                                            p->rlp, p->nrm + 1);
+                                            p->rlp, p->nrm, p->status);
         ddf_count_launch();
         ++launches;
-        DDF_CUDA_TRY(cudaMemcpyAsync(h, p->nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        // the norms and the solve's status word in one copy, one wait per step
+        DDF_CUDA_TRY(cudaMemcpyAsync(h, p->nrm, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
         DDF_CUDA_TRY(cudaStreamSynchronize(s));
         int32_t stw = 0;
-        DDF_CUDA_TRY(cudaMemcpy(&stw, p->status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        memcpy(&stw, &h[2], sizeof(int32_t));
         if (stw) {
             p->last_launches = launches;
             return (ddf_status)stw;

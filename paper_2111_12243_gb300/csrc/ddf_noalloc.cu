@@ -9,7 +9,6 @@
 // clearing; only the three header words are reset per call.  Every call on a
 // device uses the same array, so calls that overlap on the GPU race.
 #include <atomic>
-#include <mutex>
 
 #include "ddf_internal.cuh"
 
@@ -21,13 +20,9 @@ constexpr int NA_RPW = NA_CHUNK / DDF_WARPS_PER_CTA;
 
 __device__ __align__(256) uint32_t ddf_noalloc_scratch[NA_HDR + DDF_NOALLOC_MAX_ROWS];
 
-struct DeviceState {
-    uint32_t* scratch = nullptr;   // device address of ddf_noalloc_scratch on this device
-    std::atomic<uint32_t> epoch{0};
-    bool ready = false;
-};
-DeviceState g_state[64];
-std::mutex g_setup;
+// Per device ordinal: the number of the last call, so that row flags left by
+// earlier calls (which the array keeps) never match the current call's.
+std::atomic<uint32_t> g_epoch[64];
 
 __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
     uint32_t v;
@@ -116,6 +111,8 @@ k_sptrsv_noalloc(int32_t n, int64_t nnz, const int32_t* __restrict__ rp, const i
                             }
                         }
                     }
+                    // pairs with the writer's fence between its value and flag stores
+                    __threadfence_block();
                     xj = vx[lj];
                 } else {
                     if (ld_acquire_u32(flag + j) != epoch) na_wait(flag + j, epoch, hdr, cap_ns);
@@ -142,21 +139,20 @@ k_sptrsv_noalloc(int32_t n, int64_t nnz, const int32_t* __restrict__ rp, const i
     }
 }
 
-// First call on a device (with that device current): find the device address
-// of the scratch array.  In host code the array's name is only a host-side
-// stand-in, so the kernel must be given this address instead.
-ddf_status setup(int dev) {
-    std::lock_guard<std::mutex> lock(g_setup);
-    DeviceState& S = g_state[dev];
-    if (S.ready) return DDF_OK;
+// The device address of the scratch array in the current context.  In host
+// code the array's name is only a host-side stand-in, so the kernel must be
+// given this address instead.  The lookup runs on every call (it allocates
+// nothing once the module is loaded), so a context that was reset or replaced
+// since an earlier call never receives a stale address.  The first lookup in
+// a context loads the library's module, which is where the array is created.
+ddf_status scratch_address(uint32_t** out) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, ddf_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr) {
         (void)cudaGetLastError();
         return DDF_ERR_CUDA;
     }
-    S.scratch = (uint32_t*)p;
-    S.ready = true;
+    *out = (uint32_t*)p;
     return DDF_OK;
 }
 
@@ -169,31 +165,38 @@ extern "C" ddf_status ddf_sptrsv_csr_noalloc(int32_t n, int64_t nnz, const int32
     ddf_nvtx_range nvtx_("ddf_sptrsv_csr_noalloc");
     if (n < 0 || nnz < 0 || nnz > 0x7fffffffll || spin_cap_ns <= 0) return DDF_ERR_ARG;
     if (n > DDF_NOALLOC_MAX_ROWS) return DDF_ERR_TOO_LARGE;
-    if (n == 0) return DDF_OK;
-    if (!rowptr || !colidx || !values || !b || !x) return DDF_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
         (void)cudaGetLastError();
         return DDF_ERR_CUDA;
     }
-    ddf_status st = setup(dev);
+    // the set-up comes before the n == 0 return, so that an empty call is the
+    // warm-up that loads the module (and creates the array) ahead of time
+    uint32_t* scratch = nullptr;
+    ddf_status st = scratch_address(&scratch);
     if (st) return st;
-    DeviceState& S = g_state[dev];
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_sptrsv_noalloc) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return DDF_ERR_CUDA;
+    }
+    if (n == 0) return DDF_OK;
+    if (!rowptr || !colidx || !values || !b || !x) return DDF_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    uint32_t epoch = S.epoch.fetch_add(1u) + 1u;
+    uint32_t epoch = g_epoch[dev].fetch_add(1u) + 1u;
     if (epoch == 0u) {
         // the call counter wrapped: forget every old row flag once
-        DDF_CUDA_TRY(cudaMemsetAsync(S.scratch + NA_HDR, 0, sizeof(uint32_t) * DDF_NOALLOC_MAX_ROWS, s));
-        epoch = S.epoch.fetch_add(1u) + 1u;
+        DDF_CUDA_TRY(cudaMemsetAsync(scratch + NA_HDR, 0, sizeof(uint32_t) * DDF_NOALLOC_MAX_ROWS, s));
+        epoch = g_epoch[dev].fetch_add(1u) + 1u;
     }
-    DDF_CUDA_TRY(cudaMemsetAsync(S.scratch, 0, sizeof(uint32_t) * 3, s));
+    DDF_CUDA_TRY(cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * 3, s));
     const unsigned ctas = (unsigned)((n + NA_CHUNK - 1) / NA_CHUNK);
-    k_sptrsv_noalloc<<<ctas, DDF_CTA_THREADS, 0, s>>>(n, nnz, rowptr, colidx, values, b, x, S.scratch, epoch,
+    k_sptrsv_noalloc<<<ctas, DDF_CTA_THREADS, 0, s>>>(n, nnz, rowptr, colidx, values, b, x, scratch, epoch,
                                                      spin_cap_ns);
     ddf_count_launch();
     DDF_CUDA_TRY(cudaGetLastError());
     uint32_t h = 0;
-    DDF_CUDA_TRY(cudaMemcpyAsync(&h, S.scratch + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    DDF_CUDA_TRY(cudaMemcpyAsync(&h, scratch + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     DDF_CUDA_TRY(cudaStreamSynchronize(s));
     return (ddf_status)h;
 }

@@ -17,13 +17,14 @@
 namespace {
 
 constexpr char MAGIC[8] = {'D', 'D', 'F', 'P', 'L', 'A', 'N', '1'};
-constexpr int32_t VERSION = 4;
+constexpr int32_t VERSION = 5;
 
 struct Header {
     char magic[8];
     int32_t version, kind, n, n_cols, depth, has_values, vdtype, units_per_cta;
     int32_t nlevels, nblocks;
     int64_t nnz, npts, ncod, ncod_type[3], nunits[3], nchunks;
+    int64_t ntiles[2];
     ddf_opts opts;
 };
 
@@ -63,6 +64,8 @@ std::vector<Piece> pieces(ddf_plan_s* p, const Header& h, void** slots[24]) {
     add((void**)&p->part_ptr, 4 * (size_t)(h.depth + 1));
     add((void**)&p->cod, sizeof(dcod) * (size_t)h.ncod);
     for (int t = 0; t < 3; ++t) add((void**)&p->units[t], sizeof(dunit) * (size_t)h.nunits[t]);
+    if (!tr)
+        for (int t = 0; t < 2; ++t) add((void**)&p->tiles[t], sizeof(dtile) * (size_t)h.ntiles[t]);
     if (tr) {
         add((void**)&p->seq, 4 * (size_t)n);
         add((void**)&p->dinv, 8 * (size_t)n);
@@ -109,6 +112,7 @@ Header header_of(ddf_plan_s* p) {
         h.ncod_type[t] = p->ncod_type[t];
         h.nunits[t] = p->nunits[t];
     }
+    for (int t = 0; t < 2; ++t) h.ntiles[t] = p->ntiles[t];
     h.opts = p->opts;
     return h;
 }
@@ -172,7 +176,8 @@ ddf_status ddf_plan_load(const void* buf, size_t len, ddf_stream_t stream, ddf_p
     if (h.nblocks < 0 || h.nlevels < 0 || h.nchunks < 0 || h.nchunks > (int64_t)len || (h.nblocks > 0 && (h.kind != DDF_SPTRSV || h.opts.coarsen_rows < 1)))
         return DDF_ERR_ARG;
     if (h.n >= cap || h.depth >= cap || h.nblocks >= cap || h.nnz > cap || h.npts > cap || h.ncod > cap || h.nunits[0] > cap ||
-        h.nunits[1] > cap || h.nunits[2] > cap)
+        h.nunits[1] > cap || h.nunits[2] > cap || h.ntiles[0] < 0 || h.ntiles[1] < 0 || h.ntiles[0] > cap ||
+        h.ntiles[1] > cap || (h.kind == DDF_SPTRSV && h.ntiles[0] + h.ntiles[1] != 0))
         return DDF_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     ddf_plan_s* p = nullptr;
@@ -192,6 +197,7 @@ ddf_status ddf_plan_load(const void* buf, size_t len, ddf_stream_t stream, ddf_p
         p->ncod_type[t] = h.ncod_type[t];
         p->nunits[t] = h.nunits[t];
     }
+    for (int t = 0; t < 2; ++t) p->ntiles[t] = h.ntiles[t];
     if (st) {
         ddf_plan_destroy(p);
         return st;
@@ -233,10 +239,13 @@ ddf_status ddf_plan_load(const void* buf, size_t len, ddf_stream_t stream, ddf_p
         st = ddf_alloc(&p->r64, h.n, s);
         if (!st) st = ddf_alloc(&p->rlp, h.n, s);
         if (!st) st = ddf_alloc(&p->xlp, h.n, s);
-        if (!st) st = ddf_alloc(&p->nrm, 2, s);
+        if (!st) st = ddf_alloc(&p->nrm, 3, s);
     }
     if (!st && cudaStreamSynchronize(s) != cudaSuccess) st = DDF_ERR_CUDA;
     if (!st) st = ddf_plan_validate(p);
+    // derived from the validated units: the solve's unit positions
+    if (!st && h.kind == DDF_SPTRSV) st = ddf_build_unit_q(p, s);
+    if (!st && cudaStreamSynchronize(s) != cudaSuccess) st = DDF_ERR_CUDA;
     if (st) {
         (void)cudaGetLastError();
         ddf_plan_destroy(p);

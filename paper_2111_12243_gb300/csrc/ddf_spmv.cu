@@ -1,6 +1,9 @@
 // SpMV executor y = A x: one kernel per codelet type (Sec. IV-B, Listing 3).
 //
-// A warp runs one work unit (rows [i0b, i0e) of one codelet) with v lanes
+// Rows of BLAS / PSC I codelets with at most DDF_TILE_NMAX points run in
+// tiles, one lane per row (k_spmv_tile, below).  Every other codelet (PSC II,
+// and BLAS / PSC I rows longer than that) runs in work units:
+// a warp runs one work unit (rows [i0b, i0e) of one codelet) with v lanes
 // per row (v a power of two): lane li of the row group handles the points
 // i1 = li, li + v, ...; the row sum is reduced with xor shuffles inside the
 // group and written once.  The three kernels differ only in how they form
@@ -168,6 +171,75 @@ k_spmv(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64_t nu
     }
 }
 
+// Tiled rows (runs of BLAS / PSC I codelets with short rows): one lane per
+// row, no reduction.  A warp takes TILES_PER_WARP consecutive tiles of
+// DDF_TILE_ROWS rows; lane l runs row r = l % DDF_TILE_ROWS of tile
+// l / DDF_TILE_ROWS.  The tile's values are point-major, so for each point i1
+// the lanes of a tile read one contiguous stretch of w values; the column of
+// point i1 is h0 + delta*i0 + sigma*i1 (BLAS) or col[sref + i1] + delta*i0
+// (PSC I: s[i1] + h0 is the codelet's first row's column, read by every lane
+// of the codelet from the same address).  Each lane issues the loads of
+// TILE_BATCH points before using any, then one fused multiply-add per point.
+constexpr int TILES_PER_WARP = 32 / DDF_TILE_ROWS;
+constexpr int TILE_BATCH = 4;
+
+template <int TYPE, typename TV, typename TX, typename TY, typename TA>
+__global__ void __launch_bounds__(DDF_CTA_THREADS, SPMV_MIN_CTAS)
+k_spmv_tile(const dcod* __restrict__ cod, const dtile* __restrict__ tiles, int64_t ntiles,
+            const int32_t* __restrict__ col, const TV* __restrict__ val, const TX* __restrict__ x,
+            TY* __restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / DDF_TILE_ROWS, r = lane % DDF_TILE_ROWS;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t tb = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * TILES_PER_WARP; tb < ntiles;
+         tb += nw * TILES_PER_WARP) {
+        const int64_t t = tb + sub;
+        int32_t n = 0, w = 0, fr = 0;
+        const TV* vp = val;
+        const int32_t* sp = col;   // PSC I: the codelet's s (its first row's columns)
+        int32_t hb = 0, sg = 0;    // BLAS: column h0 + delta*i0 + sigma*i1; PSC I: col[sref + i1] + hb
+        if (t < ntiles) {
+            const dtile T = tiles[t];
+            w = (int32_t)(T.meta & 7u) + 1;
+            if (r < w) {
+                const dcod C = cod[T.cod + (int32_t)((T.meta >> (3 + 3 * r)) & 7u)];
+                const int32_t i0 = T.q + r - C.q0;
+                n = C.n;
+                fr = C.f0 + C.rho * i0;
+                vp = val + T.vb + r;
+                if (TYPE == DDF_BLAS) {
+                    hb = C.h0 + C.delta * i0;
+                    sg = C.sigma;
+                } else {
+                    sp = col + C.sref;
+                    hb = C.delta * i0;
+                }
+            }
+        }
+        TA acc = 0;
+        int32_t i1 = 0;
+        for (; i1 + TILE_BATCH <= n; i1 += TILE_BATCH) {
+            TV vv[TILE_BATCH];
+            int32_t jj[TILE_BATCH];
+            TX xv[TILE_BATCH];
+#pragma unroll
+            for (int k = 0; k < TILE_BATCH; ++k) {
+                jj[k] = TYPE == DDF_BLAS ? hb + sg * (i1 + k) : __ldg(sp + i1 + k) + hb;
+                vv[k] = __ldcs(vp + (int64_t)(i1 + k) * w);
+            }
+#pragma unroll
+            for (int k = 0; k < TILE_BATCH; ++k) xv[k] = __ldg(x + jj[k]);
+#pragma unroll
+            for (int k = 0; k < TILE_BATCH; ++k) acc += ddf_cvt<TA>(vv[k]) * ddf_cvt<TA>(xv[k]);
+        }
+        for (; i1 < n; ++i1) {
+            const int32_t j = TYPE == DDF_BLAS ? hb + sg * i1 : __ldg(sp + i1) + hb;
+            acc += ddf_cvt<TA>(__ldcs(vp + (int64_t)i1 * w)) * ddf_cvt<TA>(__ldg(x + j));
+        }
+        if (r < w) y[fr] = store_cvt<TY, TA>(acc);
+    }
+}
+
 unsigned grid_for(int64_t nunits, int sm_count) {
     int64_t ctas = (nunits + DDF_WARPS_PER_CTA - 1) / DDF_WARPS_PER_CTA;
     int64_t cap = (int64_t)sm_count * 32;
@@ -180,6 +252,20 @@ template <typename TV, typename TX, typename TY, typename TA>
 int launch_all(ddf_plan_s* p, const TV* val, const TX* x, TY* y, cudaStream_t s) {
     int launches = 0;
     int sm = p->sm_count > 0 ? p->sm_count : 152;
+    if (p->ntiles[DDF_BLAS] > 0) {
+        k_spmv_tile<DDF_BLAS, TV, TX, TY, TA>
+            <<<grid_for((p->ntiles[0] + TILES_PER_WARP - 1) / TILES_PER_WARP, sm), DDF_CTA_THREADS, 0, s>>>(
+                p->cod, p->tiles[0], p->ntiles[0], p->col, val, x, y);
+        ddf_count_launch();
+        ++launches;
+    }
+    if (p->ntiles[DDF_PSC1] > 0) {
+        k_spmv_tile<DDF_PSC1, TV, TX, TY, TA>
+            <<<grid_for((p->ntiles[1] + TILES_PER_WARP - 1) / TILES_PER_WARP, sm), DDF_CTA_THREADS, 0, s>>>(
+                p->cod, p->tiles[1], p->ntiles[1], p->col, val, x, y);
+        ddf_count_launch();
+        ++launches;
+    }
     if (p->nunits[DDF_BLAS] > 0) {
         k_spmv<DDF_BLAS, TV, TX, TY, TA><<<grid_for(p->nunits[0], sm), DDF_CTA_THREADS, 0, s>>>(
             p->cod, p->units[0], p->nunits[0], p->starts, p->col, val, x, y);

@@ -27,7 +27,6 @@
 
 namespace {
 
-constexpr int SMAX = 4;   // points per lane held in registers before the dependency reads
 
 // Bit-level view of the vector type: the ready-flag pattern is a NaN that
 // arithmetic never produces; a result equal to it is stored as the canonical NaN.
@@ -100,118 +99,201 @@ __device__ __forceinline__ TX dep(const TX* x, int32_t j, int32_t* status, uint3
 }
 
 // One warp per work unit; a unit is the rows one warp pass covers (32 / v
-// rows, v lanes per row).  Everything that does not depend on x (descriptor,
-// row index, values, columns, b, 1/L_ii) is loaded before the first
-// dependency is read, and the reads of all dependencies of a lane are issued
-// together, so a unit waiting on an earlier level only pays the flag hop.
+// rows, v lanes per row).  Warp gw of W runs units gw, gw + W, gw + 2W, ...
+// and software-pipelines them: what a unit needs before its dependencies can
+// be read comes through three dependent loads (the unit record and its first
+// position; then the codelet descriptor, the row, its value extent and
+// 1 / L_ii; then the values, the columns and b), so while the warp waits on
+// unit k's dependencies it already issues the third level of loads for unit
+// k+1, the second for unit k+2 and the first for unit k+3.  When unit k's
+// dependencies are ready, only their flag hop is left on the critical path.
+constexpr int SOLVE_SMAX = DDF_SOLVE_PTS;   // points per lane held in registers (rows of up to SMAX v points)
+
+struct SolveL1 {                // level 1: unit record
+    int32_t cod, i0b, i0e, v, qb;
+};
+template <typename TX>
+struct SolveL2 {                // level 2: descriptor fields, row, value extent, 1 / L_ii
+    int32_t v, li, q, act;
+    int32_t cq0, ctype, ch0, cdelta, csigma, csref;
+    int32_t r, s0, s1;
+    TX di;
+};
 template <typename TV, typename TX>
-__global__ void __launch_bounds__(DDF_CTA_THREADS, 4)
-k_sptrsv(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64_t nunits,
-         const int32_t* __restrict__ seq, const int32_t* __restrict__ st, const int32_t* __restrict__ col,
-         const TV* __restrict__ val, const TX* __restrict__ dinv, const TX* __restrict__ b, TX* x,
-         uint32_t* ticket, int32_t* status, int64_t cap_ns) {
+struct SolveL3 {                // level 3: values, columns, b
+    int32_t v, li, act, r, L, kb, hb, type, sigma, sref, h0, joff;
+    TX di, bv;
+    TV vv[SOLVE_SMAX];
+    int32_t jraw[SOLVE_SMAX];
+};
+
+__device__ __forceinline__ void solve_ld1(const dunit* __restrict__ units, const int32_t* __restrict__ unit_q,
+                                          int64_t u, int64_t nunits, SolveL1& a) {
+    if (u < nunits) {
+        const int4 t = __ldg(reinterpret_cast<const int4*>(units + u));
+        a.cod = t.x;
+        a.i0b = t.y;
+        a.i0e = t.z;
+        a.v = t.w;
+        a.qb = __ldg(unit_q + u);
+    } else {
+        a.cod = -1;
+        a.i0b = a.i0e = a.qb = 0;
+        a.v = 32;
+    }
+}
+
+template <typename TX>
+__device__ __forceinline__ void solve_ld2(const SolveL1& a, int lane, const dcod* __restrict__ cod,
+                                          const int32_t* __restrict__ seq, const int32_t* __restrict__ st,
+                                          const TX* __restrict__ dinv, SolveL2<TX>& c) {
+    const int lg = __ffs(a.v) - 1;
+    const int sub = lane >> lg;
+    c.v = a.v;
+    c.li = lane & (a.v - 1);
+    c.act = a.cod >= 0 && a.i0b + sub < a.i0e;
+    c.q = a.qb + sub;
+    c.cq0 = c.ctype = c.ch0 = c.cdelta = c.csigma = c.csref = 0;
+    c.r = c.s0 = c.s1 = 0;
+    c.di = 0;
+    if (a.cod >= 0) {
+        const dcod* C = cod + a.cod;
+        c.cq0 = __ldg(&C->q0);
+        c.ctype = __ldg(&C->type);
+        c.ch0 = __ldg(&C->h0);
+        c.cdelta = __ldg(&C->delta);
+        c.csigma = __ldg(&C->sigma);
+        c.csref = __ldg(&C->sref);
+    }
+    if (c.act) {
+        c.r = __ldg(seq + c.q);
+        c.s0 = __ldg(st + c.q);
+        c.s1 = __ldg(st + c.q + 1);
+        c.di = __ldg(dinv + c.q);
+    }
+}
+
+template <typename TV, typename TX>
+__device__ __forceinline__ void solve_ld3(const SolveL2<TX>& c, const int32_t* __restrict__ col,
+                                          const TV* __restrict__ val, const TX* __restrict__ b,
+                                          SolveL3<TV, TX>& d) {
+    d.v = c.v;
+    d.li = c.li;
+    d.act = c.act;
+    d.r = c.r;
+    d.di = c.di;
+    d.type = c.ctype;
+    d.sigma = c.csigma;
+    d.sref = c.csref;
+    d.h0 = c.ch0;
+    d.kb = c.s0;
+    d.L = c.act ? c.s1 - c.s0 : 0;
+    d.hb = c.ch0 + c.cdelta * (c.q - c.cq0);
+    d.joff = c.ctype == DDF_PSC1 ? d.hb - c.ch0 : 0;
+    d.bv = c.act ? __ldg(b + c.r) : (TX)0;
+#pragma unroll
+    for (int k = 0; k < SOLVE_SMAX; ++k) {
+        const int32_t i1 = d.li + k * d.v;
+        d.vv[k] = (TV)0;
+        d.jraw[k] = 0;
+        if (i1 < d.L) {
+            d.vv[k] = __ldg(val + d.kb + i1);
+            d.jraw[k] = d.type == DDF_BLAS   ? d.hb + d.sigma * i1
+                        : d.type == DDF_PSC1 ? __ldg(col + d.sref + i1)
+                                             : __ldg(col + d.kb + i1);
+        }
+    }
+}
+
+template <typename TV, typename TX>
+__global__ void __launch_bounds__(DDF_CTA_THREADS, DDF_SOLVE_CTAS_PER_SM)
+k_sptrsv(const dcod* __restrict__ cod, const dunit* __restrict__ units, const int32_t* __restrict__ unit_q,
+         int64_t nunits, const int32_t* __restrict__ seq, const int32_t* __restrict__ st,
+         const int32_t* __restrict__ col, const TV* __restrict__ val, const TX* __restrict__ dinv,
+         const TX* __restrict__ b, TX* x, uint32_t* ticket, int32_t* status, int64_t cap_ns) {
     using B = XBits<TX>;
     uint32_t* abort_flag = ticket + 1;
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nunits; u += nw) {
-        const dunit U = units[u];
-        const dcod C = cod[U.cod];
-        const int v = U.v;
-        const int lg = __ffs(v) - 1;
-        const int rpw = 32 >> lg;
-        const int sub = lane >> lg;
-        const int li = lane & (v - 1);
-        for (int32_t ib = U.i0b; ib < U.i0e; ib += rpw) {
-            const int32_t i0 = ib + sub;
-            const bool act = i0 < U.i0e;
-            const int32_t q = C.q0 + i0;
-            int32_t r = 0, kb = 0, L = 0, hb = 0;
-            TX bv = 0, di = 0;
-            TX vv[SMAX];
-            int32_t jj[SMAX];
+    const int64_t u0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (u0 >= nunits) return;   // warp-uniform
+    // prologue: unit 0 to level 3, unit 1 to level 2, unit 2 to level 1
+    SolveL1 t0, t1, t2;
+    solve_ld1(units, unit_q, u0, nunits, t0);
+    solve_ld1(units, unit_q, u0 + nw, nunits, t1);
+    solve_ld1(units, unit_q, u0 + 2 * nw, nunits, t2);
+    SolveL2<TX> c0, c1;
+    solve_ld2<TX>(t0, lane, cod, seq, st, dinv, c0);
+    solve_ld2<TX>(t1, lane, cod, seq, st, dinv, c1);
+    SolveL3<TV, TX> cur;
+    solve_ld3<TV, TX>(c0, col, val, b, cur);
+    for (int64_t u = u0; u < nunits; u += nw) {
+        // this unit's dependencies first
+        typename B::U xv[SOLVE_SMAX];
 #pragma unroll
-            for (int k = 0; k < SMAX; ++k) {
-                vv[k] = 0;
-                jj[k] = -1;
-            }
-            if (act) {
-                r = (C.flags & DC_F_STRIDED) ? C.f0 + C.rho * i0 : seq[q];
-                if (C.type == DDF_PSC2) {
-                    kb = st[q];
-                    L = st[q + 1] - kb;
-                } else {
-                    kb = C.g0 + C.gamma * i0;
-                    L = C.n;
+        for (int k = 0; k < SOLVE_SMAX; ++k) {
+            const int32_t i1 = cur.li + k * cur.v;
+            xv[k] = i1 < cur.L ? B::ld(x + cur.jraw[k] + cur.joff) : (typename B::U)0;
+        }
+        // then the next units' loads, which land while this unit waits
+        SolveL3<TV, TX> nxt;
+        solve_ld3<TV, TX>(c1, col, val, b, nxt);
+        SolveL2<TX> c2;
+        solve_ld2<TX>(t2, lane, cod, seq, st, dinv, c2);
+        SolveL1 t3;
+        solve_ld1(units, unit_q, u + 3 * nw, nunits, t3);
+        // While some dependencies held in registers are not ready, every lane
+        // re-reads its own missing values, so one round trip checks all of
+        // the warp's late dependencies at once.  The wait is bounded: every
+        // 16 rounds the warp checks the abort flag and the time since it
+        // started waiting, and past cap_ns it latches DDF_ERR_TIMEOUT.
+        uint64_t tw = 0;
+        uint32_t rounds = 0;
+        while (true) {
+            bool miss = false;
+#pragma unroll
+            for (int k = 0; k < SOLVE_SMAX; ++k) miss |= (cur.li + k * cur.v < cur.L) && xv[k] == B::SENT;
+            if (!__any_sync(0xffffffffu, miss)) break;
+            if (rounds == 0) tw = ddf_globaltimer();
+            ++rounds;
+            bool stop = false;
+            if ((rounds & 15u) == 0) {
+                const bool late = __any_sync(0xffffffffu, (int64_t)(ddf_globaltimer() - tw) > cap_ns);
+                if (late && lane == 0) {
+                    ddf_set_status(status, DDF_ERR_TIMEOUT);
+                    atomicExch(abort_flag, 1u);
                 }
-                hb = C.h0 + C.delta * i0;
-                bv = b[r];
-                di = dinv[q];
-#pragma unroll
-                for (int k = 0; k < SMAX; ++k) {
-                    const int32_t i1 = li + k * v;
-                    if (i1 < L) {
-                        vv[k] = ddf_cvt<TX>(val[kb + i1]);
-                        jj[k] = (C.type == DDF_BLAS)   ? hb + C.sigma * i1
-                                : (C.type == DDF_PSC1) ? hb + (col[C.sref + i1] - C.h0)
-                                                       : col[kb + i1];
-                    }
-                }
+                stop = late || __any_sync(0xffffffffu, ddf_ld_relaxed_s32(abort_flag) != 0);
             }
-            TX acc = 0;
-            // Read the dependencies held in registers; while some are not
-            // ready, every lane re-reads its own missing values, so one round
-            // trip checks all of the warp's late dependencies at once (a
-            // single poller per warp, re-reading the rest after its value
-            // arrived, needed a round trip per late dependency: 1.20 against
-            // 0.97 us per level on a chain).  The wait is bounded: every 16
-            // rounds the warp checks the abort flag and the time since it
-            // started waiting, and past cap_ns it latches DDF_ERR_TIMEOUT.
-            typename B::U xv[SMAX];
+            if (rounds > 64) __nanosleep(64);
 #pragma unroll
-            for (int k = 0; k < SMAX; ++k) xv[k] = jj[k] >= 0 ? B::ld(x + jj[k]) : (typename B::U)0;
-            uint64_t t0 = 0;
-            uint32_t rounds = 0;
-            while (true) {
-                bool miss = false;
+            for (int k = 0; k < SOLVE_SMAX; ++k)
+                if ((cur.li + k * cur.v < cur.L) && xv[k] == B::SENT)
+                    xv[k] = stop ? B::CANON : B::ld(x + cur.jraw[k] + cur.joff);
+        }
+        TX acc = 0;
+        if (cur.act) {
 #pragma unroll
-                for (int k = 0; k < SMAX; ++k) miss |= jj[k] >= 0 && xv[k] == B::SENT;
-                if (!__any_sync(0xffffffffu, miss)) break;
-                if (rounds == 0) t0 = ddf_globaltimer();
-                ++rounds;
-                bool stop = false;
-                if ((rounds & 15u) == 0) {
-                    const bool late = __any_sync(0xffffffffu, (int64_t)(ddf_globaltimer() - t0) > cap_ns);
-                    if (late && lane == 0) {
-                        ddf_set_status(status, DDF_ERR_TIMEOUT);
-                        atomicExch(abort_flag, 1u);
-                    }
-                    stop = late || __any_sync(0xffffffffu, ddf_ld_relaxed_s32(abort_flag) != 0);
-                }
-                if (rounds > 64) __nanosleep(64);
-#pragma unroll
-                for (int k = 0; k < SMAX; ++k)
-                    if (jj[k] >= 0 && xv[k] == B::SENT) xv[k] = stop ? B::CANON : B::ld(x + jj[k]);
-            }
-            if (act) {
-#pragma unroll
-                for (int k = 0; k < SMAX; ++k)
-                    if (jj[k] >= 0) acc += vv[k] * B::val(xv[k]);
-                for (int32_t i1 = li + SMAX * v; i1 < L; i1 += v) {
-                    const int32_t j = (C.type == DDF_BLAS)   ? hb + C.sigma * i1
-                                      : (C.type == DDF_PSC1) ? hb + (col[C.sref + i1] - C.h0)
-                                                             : col[kb + i1];
-                    acc += ddf_cvt<TX>(val[kb + i1]) * dep<TX>(x, j, status, abort_flag, cap_ns);
-                }
-            }
-            for (int o = v >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (act && li == 0) {
-                TX xr = (bv - acc) * di;
-                typename B::U bits = B::bits(xr);
-                if (bits == B::SENT) bits = B::CANON;
-                B::st(x + r, bits);
+            for (int k = 0; k < SOLVE_SMAX; ++k)
+                if (cur.li + k * cur.v < cur.L) acc += ddf_cvt<TX>(cur.vv[k]) * B::val(xv[k]);
+            // rows longer than SOLVE_SMAX * v points: the rest one by one
+            for (int32_t i1 = cur.li + SOLVE_SMAX * cur.v; i1 < cur.L; i1 += cur.v) {
+                const int32_t j = cur.type == DDF_BLAS   ? cur.hb + cur.sigma * i1
+                                  : cur.type == DDF_PSC1 ? cur.hb + (col[cur.sref + i1] - cur.h0)
+                                                         : col[cur.kb + i1];
+                acc += ddf_cvt<TX>(val[cur.kb + i1]) * dep<TX>(x, j, status, abort_flag, cap_ns);
             }
         }
+        for (int o = cur.v >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (cur.act && cur.li == 0) {
+            TX xr = (cur.bv - acc) * cur.di;
+            typename B::U bits = B::bits(xr);
+            if (bits == B::SENT) bits = B::CANON;
+            B::st(x + cur.r, bits);
+        }
+        cur = nxt;
+        c1 = c2;
+        t2 = t3;
     }
 }
 
@@ -642,13 +724,14 @@ ddf_status launch_solve(ddf_plan_s* p, const TV* val, const TX* dinv, const TX* 
         if (ctas > (int64_t)per_sm * sm) ctas = (int64_t)per_sm * sm;
         const dcod* a_cod = p->cod;
         const dunit* a_units = p->units[0];
+        const int32_t* a_uq = p->unit_q;
         const int32_t* a_seq = p->seq;
         const int32_t* a_st = p->starts;
         const int32_t* a_col = p->col;
         uint32_t* a_ticket = p->ticket;
         int32_t* a_status = p->status;
         int64_t a_cap = p->opts.spin_cap_ns;
-        void* args[] = {(void*)&a_cod, (void*)&a_units, (void*)&nu, (void*)&a_seq, (void*)&a_st, (void*)&a_col,
+        void* args[] = {(void*)&a_cod, (void*)&a_units, (void*)&a_uq, (void*)&nu, (void*)&a_seq, (void*)&a_st, (void*)&a_col,
                         (void*)&val, (void*)&dinv, (void*)&b, (void*)&x, (void*)&a_ticket, (void*)&a_status,
                         (void*)&a_cap};
         DDF_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_sptrsv<TV, TX>, dim3((unsigned)ctas),

@@ -5,6 +5,8 @@
 //   value extents  g: starts[q] .. starts[q+1] (PSC II) or g0 + gamma*i0, n points
 //   columns        h: h0 + delta*i0 + sigma*i1 (BLAS), h0 + delta*i0 + s[i1] (PSC I),
 //                     col[g] (PSC II), inside [0, n_cols)
+//   value tiles    (SpMV) runs of codelets of one type and row length, and
+//                  tiles whose rows lie in the codelets they name
 // and, for SpTRSV, that every column names a row solved before the row that
 // reads it: below the diagonal and in an earlier partition.  Work units must
 // name codelets and row ranges that exist.  ddf_plan_load runs this on every
@@ -47,6 +49,27 @@ __global__ void k_check_codelets(int kind, int64_t ncod, const dcod* __restrict_
         return;
     }
     const bool trsv = kind == DDF_SPTRSV;
+    if (C.flags & DC_TILED) {
+        // a run of SpMV value tiles: consecutive codelets of one type and row
+        // length, every row of length n (the tiles' values are w x n blocks)
+        bool ok = !trsv && C.type != DDF_PSC2 && C.n >= 0 && C.n <= DDF_TILE_NMAX && C.pad0 >= 0 &&
+                  C.pad0 <= C.q0 && (int64_t)C.q0 + C.m <= C.pad1 && C.pad1 <= n;
+        if (ok && C.q0 > C.pad0) {
+            const dcod P = cod[c > 0 ? c - 1 : 0];
+            ok = c > 0 && (P.flags & DC_TILED) && P.type == C.type && P.n == C.n && P.pad0 == C.pad0 &&
+                 P.pad1 == C.pad1 && P.q0 + P.m == C.q0;
+        }
+        if (ok && C.q0 + C.m < C.pad1) {
+            const dcod N = cod[c + 1 < ncod ? c + 1 : c];
+            ok = c + 1 < ncod && (N.flags & DC_TILED) && N.type == C.type && N.n == C.n && N.pad0 == C.pad0 &&
+                 N.pad1 == C.pad1 && N.q0 == C.q0 + C.m;
+        }
+        for (int32_t i0 = 0; ok && i0 < C.m; ++i0) ok = st[C.q0 + i0 + 1] - st[C.q0 + i0] == C.n;
+        if (!ok) {
+            fail(err, DDF_ERR_ARG);
+            return;
+        }
+    }
     const int32_t pstart = part_ptr[C.part];
     for (int32_t i0 = 0; i0 < C.m; ++i0) {
         const int32_t q = C.q0 + i0;
@@ -125,6 +148,34 @@ __global__ void k_check_units(int kind, int64_t ncod, const dcod* __restrict__ c
         same = same && C.type == C0.type && C.n == C0.n;
     }
     if (!same || rows != U.i0e || rows > 256) fail(err, DDF_ERR_ARG);
+}
+
+// One thread per SpMV value tile: rows inside the plan and inside the codelets
+// the tile names (tiled, of the list's type and one row length), values from
+// the first row's offset.
+__global__ void k_check_tiles(int type, int64_t ncod, const dcod* __restrict__ cod, const dtile* __restrict__ tiles,
+                              int64_t ntiles, int32_t n, const int32_t* __restrict__ st, int32_t* __restrict__ err) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const dtile T = tiles[t];
+    const int32_t w = (int32_t)(T.meta & 7u) + 1;
+    if (T.cod < 0 || T.cod >= ncod || T.q < 0 || (int64_t)T.q + w > n || T.vb != st[T.q] || (T.meta >> 27) != 0) {
+        fail(err, DDF_ERR_ARG);
+        return;
+    }
+    const int32_t n0 = cod[T.cod].n;
+    for (int32_t r = 0; r < w; ++r) {
+        const int64_t c = (int64_t)T.cod + ((T.meta >> (3 + 3 * r)) & 7u);
+        if (c >= ncod) {
+            fail(err, DDF_ERR_ARG);
+            return;
+        }
+        const dcod C = cod[c];
+        if (!(C.flags & DC_TILED) || C.type != type || C.n != n0 || T.q + r < C.q0 || T.q + r >= C.q0 + C.m) {
+            fail(err, DDF_ERR_ARG);
+            return;
+        }
+    }
 }
 
 // starts[] of every plan: 0 at the first position, never decreasing, inside
@@ -236,6 +287,12 @@ ddf_status ddf_plan_validate(ddf_plan_t p) {
             if (p->nunits[t] <= 0) continue;
             k_check_units<<<ddf_grid(p->nunits[t], 256), 256, 0, s>>>(p->kind, p->ncod, p->cod, p->units[t],
                                                                       p->nunits[t], err);
+            ddf_count_launch();
+        }
+        for (int t = 0; t < 2; ++t) {
+            if (trsv || p->ntiles[t] <= 0) continue;
+            k_check_tiles<<<ddf_grid(p->ntiles[t], 256), 256, 0, s>>>(t, p->ncod, p->cod, p->tiles[t],
+                                                                      p->ntiles[t], n, p->starts, err);
             ddf_count_launch();
         }
         if (n > 0) {

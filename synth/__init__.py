@@ -20,4 +20,5 @@ from .matrices import (  # noqa: F401
     batch,
     batch_member,
     chain,
+    banded,
 )

@@ -231,7 +231,11 @@ def powerlaw(n: int, seed: int = SEED_BASE + 3, scale: float = 2.5241, tail: flo
     del near, shift, far
     keys = np.concatenate([rows * n + cols, np.arange(n, dtype=np.int64) * (n + 1)])
     del rows, cols
-    keys = np.unique(keys)
+    # sorted distinct keys (a sort and a neighbour compare: np.unique on tens
+    # of millions of int64 keys is far slower and gives the same array)
+    keys.sort()
+    if keys.size:
+        keys = keys[np.concatenate([[True], keys[1:] != keys[:-1]])]
     r = keys // n
     c = (keys - r * n).astype(np.int32)
     del keys
@@ -300,6 +304,26 @@ def random_pattern(n_rows: int, n_cols: int, density: float, seed: int, *, diag:
     return CSR(n_rows, n_cols, rowptr.astype(np.int32), c.astype(np.int32), v)
 
 
+def banded(n: int, half_bw: int, seed: int = SEED_BASE + 6) -> CSR:
+    """Band matrix: row i holds columns max(0, i - half_bw) .. min(n - 1, i +
+    half_bw), all of them, with symmetric N(0,1) off-diagonals and a diagonal
+    of 1 + sum(|row|).  Every interior row is a run of contiguous columns one
+    further right than the row before, the pattern of a BLAS codelet."""
+    lo = np.maximum(np.arange(n, dtype=np.int64) - half_bw, 0)
+    hi = np.minimum(np.arange(n, dtype=np.int64) + half_bw, n - 1)
+    lens = hi - lo + 1
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=rowptr[1:])
+    total = int(rowptr[-1])
+    rows = np.repeat(np.arange(n, dtype=np.int64), lens)
+    cols = np.repeat(lo, lens) + (np.arange(total, dtype=np.int64) - np.repeat(rowptr[:-1], lens))
+    values = _pair_normal(np.minimum(rows, cols), np.maximum(rows, cols), n, seed)
+    colidx = cols.astype(np.int32)
+    del rows, cols
+    values = _dominant_diagonal(rowptr, colidx, values)
+    return CSR(n, n, _check_int32(rowptr), colidx, values)
+
+
 def chain(n: int) -> CSR:
     """Lower bidiagonal matrix (1 on the diagonal, -1/2 below): every row reads
     the one before it, so its dependency graph is one path of n levels."""
@@ -353,6 +377,14 @@ def _w_27pt(scale):
     return stencil_27pt(k)
 
 
+def _w_27pt_normal(scale):
+    # the 27-point pattern (one unknown per node) with symmetric N(0,1)
+    # off-diagonals and a diagonal of 1 + sum(|row|): the value variant of the
+    # precision form whose entries round in FP32 / BF16
+    k = max(4, int(round(168 * scale)))
+    return elasticity_blocks(k, seed=SEED_BASE + 5, dof=1)
+
+
 #: name -> (builder(scale), diag rule for the SpTRSV lower triangle, seed)
 WORKLOADS = {
     "lap5_64": (_w_5pt, "keep", SEED_BASE + 1),
@@ -360,6 +392,7 @@ WORKLOADS = {
     "elast3x3_64": (_w_elast, "keep", SEED_BASE + 2),
     "powerlaw_4m": (_w_powerlaw, "unit_dominant", SEED_BASE + 3),
     "st27_168": (_w_27pt, "keep", SEED_BASE + 4),
+    "st27r_168": (_w_27pt_normal, "keep", SEED_BASE + 5),
 }
 
 

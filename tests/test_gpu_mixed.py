@@ -149,3 +149,48 @@ def test_update_values_refreshes_low_precision_copies():
     lo3 = synth.CSR(lo.n_rows, lo.n_cols, lo.rowptr, lo.colidx, lo.values * 3.0)
     ref = oracle.sptrsv(lo3, b)
     assert np.linalg.norm(x.cpu().numpy() - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", ["st27_168", "st27r_168"])
+def test_precision_form_full_size(name):
+    """The precision form at its full size: the 27-point stencil on 168^3
+    (126.5M nonzeros) with integer values 26 / -1 (exact in FP32 and BF16)
+    and with N(0,1) diagonally dominant values (rounded by FP32 / BF16).
+    SpMV: every row within the FP32 accumulation bound of the oracle run on
+    the same rounded inputs, and the normwise error against the FP64 oracle
+    stated.  SpTRSV: refined to an oracle-computed relative residual <= 1e-12."""
+    a, lo, x, b = synth.workload(name)
+    y64 = oracle.spmv(a, x)
+    k = np.maximum(np.diff(a.rowptr), 1)
+    A = (dev(a.rowptr), dev(a.colidx), dev(a.values))
+    for vdt, tdt, loose in ((ddf.DDF_F32, torch.float32, 1e-6), (ddf.DDF_BF16, torch.bfloat16, 1e-2)):
+        av = rounded(a.values, vdt)
+        xv = rounded(x, vdt)
+        ar = synth.CSR(a.n_rows, a.n_cols, a.rowptr, a.colidx, av)
+        ref = oracle.spmv(ar, xv)
+        absref = oracle.spmv(synth.CSR(a.n_rows, a.n_cols, a.rowptr, a.colidx, np.abs(av)), np.abs(xv))
+        p = ddf.ddf_inspect(*A, a.n_cols, ddf.DDF_SPMV, ddf.ddf_opts_default(store_dtype=vdt))
+        y = torch.empty(a.n_rows, dtype=tdt, device="cuda")
+        ddf.ddf_spmv_lowp(p, dev(xv).to(tdt), y)
+        got = y.double().cpu().numpy()
+        bound = 2 * k * U32 * absref + 1e-30
+        if vdt == ddf.DDF_BF16:
+            bound = bound + 2.0 ** -8 * np.abs(ref)
+        assert np.all(np.abs(got - ref) <= bound)
+        assert np.linalg.norm(got - y64) <= loose * np.linalg.norm(y64)
+        del p
+    del A
+    torch.cuda.empty_cache()
+    ref_x = oracle.sptrsv(lo, b)
+    L = (dev(lo.rowptr), dev(lo.colidx), dev(lo.values))
+    for vdt in (ddf.DDF_F32, ddf.DDF_BF16):
+        q = ddf.ddf_inspect(*L, lo.n_cols, ddf.DDF_SPTRSV, ddf.ddf_opts_default(store_dtype=vdt))
+        xr = torch.zeros(lo.n_rows, dtype=torch.float64, device="cuda")
+        st, iters, rel = ddf.ddf_sptrsv_refine(q, dev(b), xr, tol=1e-12, max_iter=30)
+        assert st == 0, (ddf.ddf_status_string(st), iters, rel)
+        xs = xr.cpu().numpy()
+        assert np.linalg.norm(b - oracle.spmv(lo, xs)) <= 1e-12 * np.linalg.norm(b)
+        assert np.linalg.norm(xs - ref_x) <= 1e-10 * np.linalg.norm(ref_x)
+        del q
+    torch.cuda.empty_cache()

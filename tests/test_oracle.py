@@ -66,6 +66,25 @@ def test_spmv_empty_and_integer_exact():
     assert oracle.spmv(z, np.zeros(0)).size == 0
 
 
+@pytest.mark.parametrize("threads", [1, 2, 3, 8, 64])
+def test_spmv_parallel_equals_sequential_and_brute_force(threads):
+    # the row split must cover every row once (a skipped or doubled boundary
+    # row would differ), and each row is summed in CSR order, so the result is
+    # the sequential one bit for bit; it is also within the dot-product bound
+    # of the dense product
+    a = synth.random_pattern(97, 50, 0.2, 5, empty_rows=0.2)
+    x = synth.uniform_vector(50, 12)
+    y = oracle.spmv_par(a, x, threads)
+    assert np.array_equal(y, oracle.spmv(a, x))
+    d = dense(a)
+    assert np.allclose(y, d @ x, rtol=0, atol=1e-12)
+    z = synth.CSR(0, 0, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    assert oracle.spmv_par(z, np.zeros(0), threads).size == 0
+    p = synth.powerlaw(5000, 3)
+    xp = synth.uniform_vector(5000, 4)
+    assert np.array_equal(oracle.spmv_par(p, xp, threads), oracle.spmv(p, xp))
+
+
 def test_spmv_stencil_closed_forms():
     # A * 1 = row sums: zero on interior Laplacian rows, 6 - #neighbours on the boundary
     a = synth.laplacian_7pt(9)
