@@ -116,22 +116,11 @@ __global__ void k_i64_to_i32(const int64_t* __restrict__ in, int32_t* __restrict
 // ---------------------------------------------------------------------------
 // findDependencies: level[i] = 1 + max level of its off-diagonal columns
 // ---------------------------------------------------------------------------
-// The rows are cut into runs: a run starts at every row that does not read
-// the row just before it (the start of a grid line of a stencil, for
-// instance) and at every multiple of LEV_MAXSEG.  Each sub-warp (k_levels,
-// below) takes the next run from a global ticket and computes its rows in
-// order, so a chain that follows the rows stays on one sub-warp while the next
-// run, which only waits for the rows it reads, runs on another.  Runs are
-// taken in increasing order, and a row reads only rows with a smaller index,
-// so every row waited on belongs to a run that a running sub-warp holds or
-// has finished: the waits end (the sub-warps of one warp diverge while they
-// wait, and independent thread scheduling keeps every one of them moving;
-// each wait is still bounded by spin_cap_ns).
-constexpr int LEV_MAXSEG = 256;   // longest run one sub-warp takes at once
-constexpr int LEV_WARPS = 8;      // warps per CTA
+constexpr int LEV_CHUNK = 1024;                               // rows per CTA ticket (a multiple of 1024)
+constexpr int LEV_MAXSEG = 128;                               // longest run one warp takes at once
 
-// Bounded wait on a level written by another sub-warp: a few immediate polls,
-// then short sleeps (at most 128 ns) between polls.
+// Bounded wait on a level written by another CTA: a few immediate polls, then
+// exponential backoff so that waiting warps do not flood L2 with requests.
 __device__ int32_t wait_level(const int32_t* p, int32_t* status, int64_t cap_ns) {
     uint64_t t0 = ddf_globaltimer();
     uint32_t it = 0, ns = 32;
@@ -141,7 +130,7 @@ __device__ int32_t wait_level(const int32_t* p, int32_t* status, int64_t cap_ns)
         ++it;
         if (it > 4) {
             __nanosleep(ns);
-            ns = min(ns * 2, 128u);
+            ns = min(ns * 2, 512u);
         }
         if ((it & 15u) == 0) {
             if (ddf_ld_relaxed_s32(status) != 0) return 0;
@@ -153,142 +142,193 @@ __device__ int32_t wait_level(const int32_t* p, int32_t* status, int64_t cap_ns)
     }
 }
 
-// cut[r] = 1 when row r starts a run
-__global__ void k_lev_cut(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ re,
-                          const int32_t* __restrict__ ci, int32_t* __restrict__ cut) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    const int32_t e = re[r] - 1;   // the diagonal is last
-    cut[r] = (r % LEV_MAXSEG) == 0 || !(e > rp[r] && ci[e - 1] == (int32_t)(r - 1));
-}
-
-// rs[k] = first row of run k (from the exclusive scan of the cuts); rs[R] = n
-__global__ void k_lev_starts(int32_t n, const int32_t* __restrict__ cut, const int64_t* __restrict__ off,
-                             int32_t* __restrict__ rs) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    if (cut[r]) rs[off[r]] = (int32_t)r;
-    if (r == n - 1) rs[off[n]] = n;
-}
-
-// Along a run every row reads the row before it, so levels strictly increase
-// along the run and the largest level among a row's dependencies inside the
-// run is its predecessor's: lev[r] = 1 + max(lev[r-1], levels of the
-// dependencies before the run).  Only those outside the run are read from
-// memory.  A sub-warp of LEV_SW lanes walks a run's rows in order, lanes over
-// a row's columns; the columns of row r + LEV_DC and the external levels of
-// row r + LEV_DL are issued while row r is reduced.  Runs are handed out in
-// row order, which is not the order in which they become ready (a stencil's
-// wavefront): a sub-warp that holds a run ahead of the wavefront waits, so
-// the more runs are in flight the less the wavefront is held back.  Four runs
-// per warp keep about four times the resident warps in flight; the sub-warps
-// of a warp synchronise only among themselves.
-constexpr int LEV_SW = 8;             // lanes per run
-constexpr int LEV_PFS = 2;            // dependencies per lane prefetched (rows of up to 16 off-diagonals)
-constexpr int LEV_DC = 6;             // rows ahead whose columns are in flight
-constexpr int LEV_DL = 3;             // rows ahead whose external levels are in flight
-constexpr int LEV_XW = 2 * LEV_SW;    // rows whose extents a sub-warp holds (slides by LEV_SW)
-static_assert(LEV_SW + LEV_DC < LEV_XW, "the prefetch window stays inside the extents a sub-warp holds");
-
-__global__ void __launch_bounds__(32 * LEV_WARPS)
-k_levels(int32_t n, const int64_t* __restrict__ nruns_p, const int32_t* __restrict__ rs,
-         const int32_t* __restrict__ rp, const int32_t* __restrict__ re, const int32_t* __restrict__ ci,
-         int32_t* lev, uint32_t* ticket, int32_t* maxlev, int32_t* status, int64_t cap_ns) {
-    const int lane = threadIdx.x & 31;
-    const int sl = lane % LEV_SW;                                   // lane inside the sub-warp
-    const unsigned mask = ((1u << LEV_SW) - 1u) << (lane - sl);     // the sub-warp's lanes
-    const int64_t nruns = *nruns_p;   // number of runs (the scan's total)
-    int32_t mymax = 0;
+// Bounded wait on a level written by another warp of this CTA.  The wait
+// sleeps between polls: a warp spinning on shared memory would otherwise take
+// issue slots from the warp of its SM that computes the awaited row.
+__device__ int32_t wait_level_smem(volatile int32_t* p, int32_t* status, int64_t cap_ns) {
+    uint64_t t0 = ddf_globaltimer();
+    uint32_t it = 0;
     while (true) {
-        uint32_t u = 0;
-        if (sl == 0) u = atomicAdd(ticket, 1u);
-        u = __shfl_sync(mask, u, 0, LEV_SW);
-        if ((int64_t)u >= nruns) break;
-        const int32_t ua = rs[u], ub = rs[u + 1];
-        // row extents: lane sl holds rows r0 + sl and r0 + LEV_SW + sl
-        int32_t xa0 = 0, xb0 = 0, xa1 = 0, xb1 = 0;
-        int32_t r0 = ua;
-        if (r0 + sl < ub) {
-            xa0 = rp[r0 + sl];
-            xb0 = re[r0 + sl] - 1;   // the diagonal is last: not a dependency
-        }
-        if (r0 + LEV_SW + sl < ub) {
-            xa1 = rp[r0 + LEV_SW + sl];
-            xb1 = re[r0 + LEV_SW + sl] - 1;
-        }
-        // columns (cj) and external levels (cl) of rows r .. r + LEV_DC
-        int32_t cj[LEV_DC + 1][LEV_PFS], cl[LEV_DL + 1][LEV_PFS];
-        auto cols_of = [&](int32_t i, int32_t* j) {   // i = row offset from r0, 0 <= i < LEV_XW
-            const int32_t a = __shfl_sync(mask, i < LEV_SW ? xa0 : xa1, i % LEV_SW, LEV_SW);
-            const int32_t b = __shfl_sync(mask, i < LEV_SW ? xb0 : xb1, i % LEV_SW, LEV_SW);
-#pragma unroll
-            for (int k = 0; k < LEV_PFS; ++k) {
-                const int32_t kk = a + sl + LEV_SW * k;
-                j[k] = (r0 + i < ub && kk < b) ? __ldg(ci + kk) : -1;
+        int32_t v = *p;
+        if (v >= 0) return v;
+        if (++it > 32) __nanosleep(32);
+        if ((it & 63u) == 0) {
+            if (ddf_ld_relaxed_s32(status) != 0) return 0;
+            if ((int64_t)(ddf_globaltimer() - t0) > cap_ns) {
+                ddf_set_status(status, DDF_ERR_TIMEOUT);
+                return 0;
             }
-        };
-        auto levs_of = [&](const int32_t* j, int32_t* l) {
-#pragma unroll
-            for (int k = 0; k < LEV_PFS; ++k)
-                l[k] = (j[k] >= 0 && j[k] < ua) ? ddf_ld_relaxed_s32(lev + j[k]) : -1;
-        };
-#pragma unroll
-        for (int d = 0; d <= LEV_DC; ++d) cols_of(d, cj[d]);
-#pragma unroll
-        for (int d = 0; d <= LEV_DL; ++d) levs_of(cj[d], cl[d]);
-        int32_t prev = -1;
-        for (int32_t r = ua; r < ub; ++r) {
-            int32_t i = r - r0;
-            if (i == LEV_SW) {   // slide the extent window
-                r0 += LEV_SW;
-                i = 0;
-                xa0 = xa1;
-                xb0 = xb1;
-                xa1 = xb1 = 0;
-                if (r0 + LEV_SW + sl < ub) {
-                    xa1 = rp[r0 + LEV_SW + sl];
-                    xb1 = re[r0 + LEV_SW + sl] - 1;
-                }
-            }
-            // row r: external dependencies, then the predecessor
-            int32_t m = prev;
-#pragma unroll
-            for (int k = 0; k < LEV_PFS; ++k) {
-                const int32_t jj = cj[0][k];
-                if (jj < 0 || jj >= ua) continue;
-                int32_t lj = cl[0][k];
-                if (lj < 0) lj = wait_level(lev + jj, status, cap_ns);
-                m = max(m, lj);
-            }
-            {
-                const int32_t a = __shfl_sync(mask, xa0, i, LEV_SW), b = __shfl_sync(mask, xb0, i, LEV_SW);
-                for (int32_t k = a + sl + LEV_SW * LEV_PFS; k < b; k += LEV_SW) {   // rows longer than the prefetch
-                    const int32_t jj = ci[k];
-                    if (jj >= ua) continue;
-                    int32_t lj = ddf_ld_relaxed_s32(lev + jj);
-                    if (lj < 0) lj = wait_level(lev + jj, status, cap_ns);
-                    m = max(m, lj);
-                }
-            }
-#pragma unroll
-            for (int o = LEV_SW / 2; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(mask, m, o, LEV_SW));
-            prev = m + 1;
-            if (sl == 0) ddf_st_relaxed_s32(lev + r, prev);
-            mymax = max(mymax, prev);
-            // rotate the windows and issue the loads of the rows further ahead
-#pragma unroll
-            for (int d = 0; d < LEV_DC; ++d)
-#pragma unroll
-                for (int k = 0; k < LEV_PFS; ++k) cj[d][k] = cj[d + 1][k];
-#pragma unroll
-            for (int d = 0; d < LEV_DL; ++d)
-#pragma unroll
-                for (int k = 0; k < LEV_PFS; ++k) cl[d][k] = cl[d + 1][k];
-            cols_of(i + 1 + LEV_DC, cj[LEV_DC]);
-            levs_of(cj[LEV_DL], cl[LEV_DL]);
         }
     }
-    atomicMax(maxlev, mymax);
+}
+
+// Each CTA takes the next chunk of LEV_CHUNK consecutive rows from a ticket and
+// cuts it into runs: a run starts at every row that does not read the row just
+// before it (the start of a grid line of a stencil, for instance) and at least
+// every LEV_MAXSEG rows.  Warps take runs in increasing order from a counter
+// and compute a run's rows in order, so a chain that follows the rows stays on
+// one warp while the next run, which only waits for the rows it reads, starts
+// on another.  Levels of the chunk's rows are also kept in shared memory: a
+// dependency inside the chunk costs a shared-memory read instead of an L2
+// round trip.  Rows are software pipelined: while row r is reduced, the
+// column indices of row r + 1 and the levels of its dependencies outside the
+// chunk are already in flight.  Every row waited on has a smaller index, so it
+// belongs to a run that a running warp has taken, or to a CTA that already
+// holds a ticket and runs: the waits end.  Large chunks keep many rows in
+// flight per resident thread: with one row per thread too few planes of a
+// 3-D stencil are resident for the wavefront to pipeline.
+constexpr int LEV_WARPS = 16;                                 // warps per CTA
+
+constexpr int LEV_PF = 2;   // dependencies per lane prefetched (rows of up to 64 off-diagonals)
+
+__device__ __forceinline__ void lev_prefetch(int32_t a, int32_t b, int lane, int64_t base,
+                                             const int32_t* __restrict__ ci, const int32_t* lev,
+                                             int32_t* j, int32_t* l) {
+#pragma unroll
+    for (int k = 0; k < LEV_PF; ++k) {
+        const int32_t kk = a + lane + 32 * k;
+        j[k] = kk < b ? ci[kk] : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < LEV_PF; ++k)
+        l[k] = (j[k] >= 0 && (int64_t)j[k] < base) ? ddf_ld_relaxed_s32(lev + j[k]) : -1;
+}
+
+__global__ void __launch_bounds__(32 * LEV_WARPS)
+k_levels(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ re, const int32_t* __restrict__ ci,
+         int32_t* lev, uint32_t* ticket, int32_t* maxlev, int32_t* status, int64_t cap_ns) {
+    __shared__ int32_t chunk, nruns, next;
+    __shared__ int32_t wmax[LEV_WARPS];
+    __shared__ int32_t slev[LEV_CHUNK];
+    __shared__ uint32_t scut[LEV_CHUNK / 32];
+    __shared__ int32_t rstart[LEV_CHUNK + 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        chunk = (int32_t)atomicAdd(ticket, 1u);
+        next = 0;
+    }
+    for (int i = threadIdx.x; i < LEV_CHUNK; i += blockDim.x) slev[i] = -1;
+    __syncthreads();
+    const int64_t base = (int64_t)chunk * LEV_CHUNK;
+    const int32_t rlen = (int32_t)min((int64_t)LEV_CHUNK, (int64_t)n - base);
+    // run starts: rows that do not read the previous row, and every LEV_MAXSEG rows
+    for (int bt = w; bt < LEV_CHUNK / 32; bt += LEV_WARPS) {
+        const int32_t o = bt * 32 + lane;
+        bool cut = false;
+        if (o < rlen) {
+            const int64_t r = base + o;
+            const int32_t e = re[r] - 1;   // the diagonal is last
+            cut = (o % LEV_MAXSEG) == 0 || !(e > rp[r] && ci[e - 1] == (int32_t)(r - 1));
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, cut);
+        if (lane == 0) scut[bt] = m;
+    }
+    __syncthreads();
+    if (w == 0) {
+        // positions of the set bits, in order (LEV_WPL consecutive words per lane)
+        constexpr int LEV_WPL = LEV_CHUNK / 1024;
+        int c = 0;
+#pragma unroll
+        for (int i = 0; i < LEV_WPL; ++i) c += __popc(scut[lane * LEV_WPL + i]);
+        int pre = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= o) pre += t;
+        }
+        int k = pre - c;
+#pragma unroll
+        for (int i = 0; i < LEV_WPL; ++i)
+            for (uint32_t m = scut[lane * LEV_WPL + i]; m; m &= m - 1)
+                rstart[k++] = 32 * (lane * LEV_WPL + i) + __ffs(m) - 1;
+        if (lane == 31) {
+            nruns = pre;
+            rstart[pre] = rlen;
+        }
+    }
+    __syncthreads();
+    volatile int32_t* vs = slev;
+    int32_t mymax = 0;
+    while (true) {
+        int32_t u = 0;
+        if (lane == 0) u = atomicAdd(&next, 1);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= nruns) break;
+        const int32_t ua = rstart[u], ub = rstart[u + 1];
+        for (int32_t sb = ua; sb < ub; sb += 32) {
+            // row extents of the next (up to) 32 rows of the run, one per lane
+            const int64_t r0 = base + sb;
+            const int cnt = min(32, ub - sb);
+            int32_t ra_l = 0, rb_l = 0;
+            if (lane < cnt) {
+                ra_l = rp[r0 + lane];
+                rb_l = re[r0 + lane] - 1;   // the diagonal is last: not a dependency
+            }
+            int32_t cj[LEV_PF], cl[LEV_PF];
+            {
+                const int32_t a = __shfl_sync(0xffffffffu, ra_l, 0), b = __shfl_sync(0xffffffffu, rb_l, 0);
+                lev_prefetch(a, b, lane, base, ci, lev, cj, cl);
+            }
+            for (int rr = 0; rr < cnt; ++rr) {
+                const int64_t r = r0 + rr;
+                const int32_t a = __shfl_sync(0xffffffffu, ra_l, rr), b = __shfl_sync(0xffffffffu, rb_l, rr);
+                // next row's columns and external levels go out now
+                int32_t nj[LEV_PF], nl[LEV_PF];
+                {
+                    const bool more = rr + 1 < cnt;
+                    const int32_t na = __shfl_sync(0xffffffffu, ra_l, (rr + 1) & 31);
+                    const int32_t nb = __shfl_sync(0xffffffffu, rb_l, (rr + 1) & 31);
+                    lev_prefetch(na, more ? nb : na, lane, base, ci, lev, nj, nl);
+                }
+                int32_t m = -1;
+#pragma unroll
+                for (int k = 0; k < LEV_PF; ++k) {
+                    const int32_t jj = cj[k];
+                    if (jj < 0) continue;
+                    int32_t lj;
+                    if ((int64_t)jj >= base) {
+                        lj = vs[jj - base];
+                        if (lj < 0) lj = wait_level_smem(vs + (jj - base), status, cap_ns);
+                    } else {
+                        lj = cl[k];
+                        if (lj < 0) lj = wait_level(lev + jj, status, cap_ns);
+                    }
+                    m = max(m, lj);
+                }
+                for (int32_t k = a + lane + 32 * LEV_PF; k < b; k += 32) {   // rows longer than the prefetch
+                    const int32_t jj = ci[k];
+                    int32_t lj;
+                    if ((int64_t)jj >= base) {
+                        lj = vs[jj - base];
+                        if (lj < 0) lj = wait_level_smem(vs + (jj - base), status, cap_ns);
+                    } else {
+                        lj = ddf_ld_relaxed_s32(lev + jj);
+                        if (lj < 0) lj = wait_level(lev + jj, status, cap_ns);
+                    }
+                    m = max(m, lj);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if (lane == 0) {
+                    vs[r - base] = m + 1;
+                    ddf_st_relaxed_s32(lev + r, m + 1);
+                }
+                mymax = max(mymax, m + 1);
+                __syncwarp();
+#pragma unroll
+                for (int k = 0; k < LEV_PF; ++k) {
+                    cj[k] = nj[k];
+                    cl[k] = nl[k];
+                }
+            }
+        }
+    }
+    if (lane == 0) wmax[w] = mymax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t t = 0;
+        for (int k = 0; k < LEV_WARPS; ++k) t = max(t, wmax[k]);
+        atomicMax(maxlev, t);
+    }
 }
 
 // part_ptr[l] = first position of level l in the sorted order (every level
@@ -1063,6 +1103,24 @@ __global__ void k_unit_write(int64_t ncod, const dcod* __restrict__ cod, const i
     make_units<true>(c, (int32_t)i, st, unit_nnz, !split_types, dst);
 }
 
+__device__ __forceinline__ bool long_unit(const dunit& U, const dcod* __restrict__ cod,
+                                          const int32_t* __restrict__ st) {
+    if (U.i0b < 0 || U.i0e - U.i0b != 1) return false;
+    const int32_t q = cod[U.cod].q0 + U.i0b;
+    return st[q + 1] - st[q] > DDF_LONG_ROW;
+}
+__global__ void k_long_flags(int64_t nu, const dunit* __restrict__ units, const dcod* __restrict__ cod,
+                             const int32_t* __restrict__ st, int32_t* __restrict__ flag) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < nu) flag[u] = long_unit(units[u], cod, st);
+}
+__global__ void k_long_write(int64_t nu, const dunit* __restrict__ units, const dcod* __restrict__ cod,
+                             const int32_t* __restrict__ flag, const int64_t* __restrict__ off,
+                             int32_t* __restrict__ lq) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < nu && flag[u]) lq[off[u]] = cod[units[u].cod].q0 + units[u].i0b;
+}
+
 __global__ void k_unit_q(int64_t nu, const dunit* __restrict__ units, const dcod* __restrict__ cod,
                          int32_t* __restrict__ uq) {
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1318,36 +1376,17 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
         int32_t* lev = nullptr;
         uint32_t* tick = nullptr;
         int32_t* maxlev = nullptr;
-        int32_t* cut = nullptr;
-        int64_t* coff = nullptr;
-        int32_t* rs = nullptr;
         TRY(tmp.get(&lev, n));
         TRY(tmp.get(&tick, 1));
         TRY(tmp.get(&maxlev, 2));   // [0] largest level, [1] a copy of the status word
-        TRY(tmp.get(&cut, n));
-        TRY(tmp.get(&coff, (int64_t)n + 1));
-        TRY(tmp.get(&rs, (int64_t)n + 1));
         k_fill_i32<<<ddf_grid(n, TPB, 4096), TPB, 0, s>>>(lev, n, -1);
         ddf_count_launch();
         DDF_CUDA_TRY(cudaMemsetAsync(tick, 0, sizeof(uint32_t), s));
         DDF_CUDA_TRY(cudaMemsetAsync(maxlev, 0, sizeof(int32_t), s));
         DDF_CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(int32_t), s));
         if (n > 0) {
-            // runs: rows that read the row before them continue the run
-            k_lev_cut<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, rowptr, rowend, colidx, cut);
-            ddf_count_launch();
-            TRY(ddf_scan_i32_to_i64(cut, coff, n, s));
-            k_lev_starts<<<ddf_grid(n, TPB), TPB, 0, s>>>(n, cut, coff, rs);
-            ddf_count_launch();
-            // as many warps as are resident (at most one per run), each taking
-            // runs from the ticket until none are left
-            int per_sm = 0;
-            DDF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_levels, 32 * LEV_WARPS, 0));
-            const int sm = p->sm_count > 0 ? p->sm_count : 152;
-            const int64_t want = ((int64_t)n + LEV_WARPS - 1) / LEV_WARPS;
-            const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)std::max(per_sm, 1) * sm));
-            k_levels<<<(unsigned)ctas, 32 * LEV_WARPS, 0, s>>>(n, coff + n, rs, rowptr, rowend, colidx, lev,
-                                                               tick, maxlev, p->status, p->opts.spin_cap_ns);
+            k_levels<<<ddf_grid(n, LEV_CHUNK), 32 * LEV_WARPS, 0, s>>>(n, rowptr, rowend, colidx, lev, tick,
+                                                                       maxlev, p->status, p->opts.spin_cap_ns);
             ddf_count_launch();
         }
         DDF_CUDA_TRY(cudaGetLastError());
@@ -1662,8 +1701,41 @@ ddf_status ddf_build_units(ddf_plan_s* p, cudaStream_t s) {
         ddf_count_launch();
     }
     DDF_CUDA_TRY(cudaGetLastError());
-    if (split) TRY(build_tiles(p, s));
-    else TRY(ddf_build_unit_q(p, s));
+    if (split) {
+        TRY(build_tiles(p, s));
+        TRY(ddf_build_long_rows(p, s));
+    } else {
+        TRY(ddf_build_unit_q(p, s));
+    }
+    return DDF_OK;
+}
+
+// SpMV: the PSC II rows of more than DDF_LONG_ROW points, in unit order (each
+// is a one-row unit: a unit closes before a row that would take it past
+// unit_nnz points).
+ddf_status ddf_build_long_rows(ddf_plan_s* p, cudaStream_t s) {
+    Scratch tmp{s, {}};
+    ddf_free(p->long_q, s);
+    p->nlong = 0;
+    const int64_t nu = p->nunits[2];
+    if (p->kind != DDF_SPMV || nu <= 0) return DDF_OK;
+    int32_t* flag = nullptr;
+    int64_t* off = nullptr;
+    TRY(tmp.get(&flag, nu));
+    TRY(tmp.get(&off, nu + 1));
+    k_long_flags<<<ddf_grid(nu, TPB), TPB, 0, s>>>(nu, p->units[2], p->cod, p->starts, flag);
+    ddf_count_launch();
+    DDF_CUDA_TRY(cudaGetLastError());
+    TRY(ddf_scan_i32_to_i64(flag, off, nu, s));
+    int64_t nl = 0;
+    TRY(d2h(&nl, off + nu, 1, s));
+    p->nlong = nl;
+    TRY(ddf_alloc(&p->long_q, nl, s));
+    if (nl > 0) {
+        k_long_write<<<ddf_grid(nu, TPB), TPB, 0, s>>>(nu, p->units[2], p->cod, flag, off, p->long_q);
+        ddf_count_launch();
+    }
+    DDF_CUDA_TRY(cudaGetLastError());
     return DDF_OK;
 }
 

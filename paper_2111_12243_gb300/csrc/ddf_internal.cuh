@@ -60,6 +60,7 @@ enum { DC_F_STRIDED = 1, DC_G_STRIDED = 2, DC_TILED = 4 };
 // per point.
 #define DDF_TILE_ROWS 8
 #define DDF_TILE_NMAX 256
+#define DDF_LONG_ROW 1024   // SpMV PSC II rows longer than this run one CTA per row
 
 // One tile of the SpMV executor: rows q .. q + w - 1, values from vb (the
 // tile's first row's CSR offset); row q + r belongs to codelet
@@ -105,6 +106,9 @@ struct ddf_plan_s {
                                   // units[0] = all, level order
     int64_t nunits[3];
     int32_t* unit_q;              // SpTRSV: first position of each unit of units[0]
+    int32_t* long_q;              // SpMV: positions of the PSC II rows of more than DDF_LONG_ROW
+                                  // points (each a one-row unit of units[2], run one CTA per row)
+    int64_t nlong;
     dtile* tiles[2];              // SpMV: tiles of tiled BLAS / PSC I codelets (DC_TILED)
     int64_t ntiles[2];
     // device scratch / status
@@ -216,6 +220,7 @@ ddf_status ddf_compute_stats(ddf_plan_s* p);
 ddf_status ddf_build_units(ddf_plan_s* p, cudaStream_t s);
 ddf_status ddf_mark_tiles(ddf_plan_s* p, cudaStream_t s);
 ddf_status ddf_build_unit_q(ddf_plan_s* p, cudaStream_t s);
+ddf_status ddf_build_long_rows(ddf_plan_s* p, cudaStream_t s);
 // ddf_capi.cu
 ddf_status ddf_new_plan(ddf_kind kind, const ddf_opts* o, cudaStream_t s, int32_t n, int32_t n_cols, int64_t nnz,
                         ddf_plan_s** out);

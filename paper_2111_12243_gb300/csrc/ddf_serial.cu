@@ -243,8 +243,10 @@ ddf_status ddf_plan_load(const void* buf, size_t len, ddf_stream_t stream, ddf_p
     }
     if (!st && cudaStreamSynchronize(s) != cudaSuccess) st = DDF_ERR_CUDA;
     if (!st) st = ddf_plan_validate(p);
-    // derived from the validated units: the solve's unit positions
+    // derived from the validated units: the solve's unit positions, the
+    // SpMV's long PSC II rows
     if (!st && h.kind == DDF_SPTRSV) st = ddf_build_unit_q(p, s);
+    if (!st && h.kind == DDF_SPMV) st = ddf_build_long_rows(p, s);
     if (!st && cudaStreamSynchronize(s) != cudaSuccess) st = DDF_ERR_CUDA;
     if (st) {
         (void)cudaGetLastError();

@@ -240,6 +240,83 @@ k_spmv_tile(const dcod* __restrict__ cod, const dtile* __restrict__ tiles, int64
     }
 }
 
+// PSC II units (whole consecutive rows, at most unit_nnz points): the warp
+// first forms the products val[k] * x[col[k]] of all the unit's points, lanes
+// over consecutive points (coalesced values and columns), into shared memory;
+// then each lane adds up whole rows from there.  One multiply and one add per
+// point and no shuffle reduction; a row's sum runs in point order.  Units of
+// more than PSC2_STAGE points (one row each, since a unit closes before a row
+// that would take it past unit_nnz) run the row with all 32 lanes and one
+// shuffle reduction; rows of more than DDF_LONG_ROW points are left to
+// k_spmv_long.
+constexpr int PSC2_STAGE = 256;   // points of one unit staged in shared memory
+
+template <typename TV, typename TX, typename TY, typename TA>
+__global__ void __launch_bounds__(DDF_CTA_THREADS, SPMV_MIN_CTAS)
+k_spmv_psc2(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64_t nunits,
+            const int32_t* __restrict__ st, const int32_t* __restrict__ col, const TV* __restrict__ val,
+            const TX* __restrict__ x, TY* __restrict__ y) {
+    __shared__ TA prod_all[DDF_WARPS_PER_CTA][PSC2_STAGE];
+    const int lane = threadIdx.x & 31;
+    TA* prod = prod_all[threadIdx.x >> 5];
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nunits; u += nw) {
+        const dunit U = units[u];
+        const dcod C = cod[U.cod];
+        const int32_t qa = C.q0 + U.i0b, qb = C.q0 + U.i0e;
+        const int32_t ka = st[qa], kb = st[qb];
+        const int32_t T = kb - ka;
+        if (T > PSC2_STAGE) {
+            if (T > DDF_LONG_ROW) continue;   // one CTA per row (k_spmv_long)
+            TA acc = 0;
+#pragma unroll 4
+            for (int32_t k = ka + lane; k < kb; k += 32)
+                acc += ddf_cvt<TA>(__ldcs(val + k)) * ddf_cvt<TA>(__ldg(x + __ldcs(col + k)));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) y[C.f0 + C.rho * U.i0b] = store_cvt<TY, TA>(acc);
+            continue;
+        }
+#pragma unroll 4
+        for (int32_t e = lane; e < T; e += 32)
+            prod[e] = ddf_cvt<TA>(__ldcs(val + ka + e)) * ddf_cvt<TA>(__ldg(x + __ldcs(col + ka + e)));
+        __syncwarp();
+        for (int32_t q = qa + lane; q < qb; q += 32) {
+            const int32_t a = st[q] - ka, b = st[q + 1] - ka;
+            TA acc = 0;
+            for (int32_t k = a; k < b; ++k) acc += prod[k];
+            y[C.f0 + C.rho * (q - C.q0)] = store_cvt<TY, TA>(acc);
+        }
+        __syncwarp();
+    }
+}
+
+// PSC II rows of more than DDF_LONG_ROW points: one CTA per row, threads over
+// the row's points, then a reduction in a fixed order (shuffles inside each
+// warp, warps in index order), so the result does not depend on scheduling.
+template <typename TV, typename TX, typename TY, typename TA>
+__global__ void __launch_bounds__(DDF_CTA_THREADS)
+k_spmv_long(const int32_t* __restrict__ long_q, const int32_t* __restrict__ st, const int32_t* __restrict__ col,
+            const TV* __restrict__ val, const TX* __restrict__ x, TY* __restrict__ y) {
+    __shared__ TA part[DDF_WARPS_PER_CTA];
+    const int32_t q = long_q[blockIdx.x];
+    const int32_t a = st[q], b = st[q + 1];
+    TA acc = 0;
+#pragma unroll 4
+    for (int32_t k = a + (int32_t)threadIdx.x; k < b; k += DDF_CTA_THREADS)
+        acc += ddf_cvt<TA>(__ldcs(val + k)) * ddf_cvt<TA>(__ldg(x + __ldcs(col + k)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        TA t = 0;
+#pragma unroll
+        for (int w = 0; w < DDF_WARPS_PER_CTA; ++w) t += part[w];
+        y[q] = store_cvt<TY, TA>(t);   // SpMV positions are the rows
+    }
+}
+
 unsigned grid_for(int64_t nunits, int sm_count) {
     int64_t ctas = (nunits + DDF_WARPS_PER_CTA - 1) / DDF_WARPS_PER_CTA;
     int64_t cap = (int64_t)sm_count * 32;
@@ -278,8 +355,14 @@ int launch_all(ddf_plan_s* p, const TV* val, const TX* x, TY* y, cudaStream_t s)
         ddf_count_launch();
         ++launches;
     }
+    if (p->nlong > 0) {
+        k_spmv_long<TV, TX, TY, TA><<<(unsigned)p->nlong, DDF_CTA_THREADS, 0, s>>>(p->long_q, p->starts, p->col,
+                                                                               val, x, y);
+        ddf_count_launch();
+        ++launches;
+    }
     if (p->nunits[DDF_PSC2] > 0) {
-        k_spmv<DDF_PSC2, TV, TX, TY, TA><<<grid_for(p->nunits[2], sm), DDF_CTA_THREADS, 0, s>>>(
+        k_spmv_psc2<TV, TX, TY, TA><<<grid_for(p->nunits[2], sm), DDF_CTA_THREADS, 0, s>>>(
             p->cod, p->units[2], p->nunits[2], p->starts, p->col, val, x, y);
         ddf_count_launch();
         ++launches;

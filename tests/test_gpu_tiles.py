@@ -1,11 +1,12 @@
-"""SpMV value tiles on the GPU against the CPU oracle.
+"""SpMV executor layouts on the GPU against the CPU oracle.
 
 Runs of BLAS / PSC I codelets with short rows are executed one lane per row,
 their values stored point-major in tiles of 8 rows.  These tests cover the
 shapes that exercise that layout: runs whose length is not a multiple of the
 tile (ragged last tiles), tiles that span several small codelets (3-row
 elasticity codelets), rows longer than the tile limit (which stay on the
-work-unit path), empty rows, values supplied after inspection, low-precision
+work-unit path), empty rows, PSC II rows from one point to thousands (staged
+products, one warp per row, one CTA per row), values supplied after inspection, low-precision
 copies, the multi-RHS executor, plan save / load and validation.  Results must
 match the oracle's CSR-order definitions within 1e-12 (FP64), exactly where
 every partial sum is an integer.
@@ -68,6 +69,22 @@ def with_long_rows(n=600, long_len=300, seed=4):
     return synth.CSR(n, n, rp.astype(np.int32), ci, v)
 
 
+def long_psc2_rows(n=6000, seed=8):
+    """Irregular rows (PSC II) of lengths 1 .. 5000: a few longer than 1024
+    points (one CTA per row), some between 256 and 1024 (one warp), the rest
+    short (staged products), and empty rows."""
+    rng = np.random.default_rng(seed)
+    lens = rng.integers(1, 12, n)
+    lens[rng.choice(n, 12, replace=False)] = rng.integers(1025, 5000, 12)
+    lens[rng.choice(n, 20, replace=False)] = rng.integers(257, 1024, 20)
+    lens[rng.choice(n, 30, replace=False)] = 0
+    rows = [np.sort(rng.choice(n, int(k), replace=False)) for k in lens]
+    rp = np.zeros(n + 1, np.int64)
+    rp[1:] = np.cumsum(lens)
+    ci = np.concatenate(rows).astype(np.int32)
+    return synth.CSR(n, n, rp.astype(np.int32), ci, rng.standard_normal(ci.size))
+
+
 CASES = {
     "band_1000": lambda: synth.banded(1000, 4),
     "band_29": lambda: synth.banded(29, 2),
@@ -79,6 +96,7 @@ CASES = {
     "long_rows": with_long_rows,
     "random_500": lambda: synth.random_pattern(500, 450, 0.02, 3, empty_rows=0.2),
     "powerlaw_3000": lambda: synth.powerlaw(3000),
+    "long_psc2": long_psc2_rows,
 }
 
 
@@ -120,7 +138,7 @@ def test_values_after_inspection_and_updates():
 
 
 @pytest.mark.parametrize("dtype,tol", [(ddf.DDF_F32, 2e-6), (ddf.DDF_BF16, 2e-2)])
-@pytest.mark.parametrize("name", ["st27_13", "long_rows", "elast_6"])
+@pytest.mark.parametrize("name", ["st27_13", "long_rows", "elast_6", "long_psc2"])
 def test_low_precision_tiles(dtype, tol, name):
     a = CASES[name]()
     x = synth.uniform_vector(a.n_cols, 9)
@@ -138,7 +156,7 @@ def test_low_precision_tiles(dtype, tol, name):
     assert relerr(yl.double().cpu().numpy(), ref) <= tol
 
 
-@pytest.mark.parametrize("name", ["st27_10", "long_rows", "elast_6"])
+@pytest.mark.parametrize("name", ["st27_10", "long_rows", "elast_6", "long_psc2"])
 def test_multi_rhs_on_tiled_plan(name):
     a = CASES[name]()
     nrhs = 5
@@ -172,3 +190,17 @@ def test_tiles_do_not_change_the_canonical_plan():
         ref = oracle.inspect(a, oracle.SPMV, weights=(8, 32, 4))
         assert np.array_equal(got["records"], ref.records)
         assert np.array_equal(got["gs"], ref.gs)
+
+
+def test_long_psc2_rows_are_deterministic():
+    a = long_psc2_rows(5500, 9)
+    x = synth.uniform_vector(a.n_cols, 13)
+    p = ddf.ddf_inspect(dev(a.rowptr), dev(a.colidx), dev(a.values), a.n_cols, ddf.DDF_SPMV)
+    st = ddf.ddf_plan_stats(p)
+    assert st["max_row_len"] > 1024
+    y0 = spmv(p, x, a.n_rows)
+    for _ in range(3):
+        assert np.array_equal(spmv(p, x, a.n_rows).view(np.uint64), y0.view(np.uint64))
+    assert relerr(y0, oracle.spmv(a, x)) <= TOL
+    q = ddf.ddf_plan_load(ddf.ddf_plan_save(p), a.n_rows, a.n_cols, ddf.DDF_SPMV)
+    assert np.array_equal(spmv(q, x, a.n_rows).view(np.uint64), y0.view(np.uint64))
