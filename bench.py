@@ -770,22 +770,18 @@ def run_banded(args, ddf, torch, dev, timed, hbm, n=1 << 22, half_bw=8):
 
 
 def run_e2e(args, D, ddf, torch, dev, stream, exec_b, world):
-    """Same step from pinned host buffers: CSR, x and b copied in, y and x read
-    back.  Where L is A's lower triangle with A's own diagonal (the stencil
-    workloads), only A is copied and the SpTRSV inspection reads L inside it
-    (lower_of_input), as a user holding A would call it."""
+    """Same step from pinned host buffers: CSR, x and b copied in, y and x read back."""
     H = []
     h2d = d2h = 0
     for d in D:
         a, lo = d["a"], d["lo"]
-        in_a = synth.WORKLOADS[d["name"]][1] == "keep"
         pin = lambda v: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()  # noqa: E731
         H.append({"A": (pin(a.rowptr), pin(a.colidx), pin(a.values)),
-                  "L": None if in_a else (pin(lo.rowptr), pin(lo.colidx), pin(lo.values)),
+                  "L": (pin(lo.rowptr), pin(lo.colidx), pin(lo.values)),
                   "x": pin(d["xh"]), "b": pin(d["bh"]),
                   "y": torch.empty(a.n_rows, dtype=torch.float64).pin_memory(),
                   "xs": torch.empty(lo.n_rows, dtype=torch.float64).pin_memory()})
-        h2d += csr_bytes(a) + (0 if in_a else csr_bytes(lo)) + 8 * a.n_cols + 8 * lo.n_rows
+        h2d += csr_bytes(a) + csr_bytes(lo) + 8 * a.n_cols + 8 * lo.n_rows
         d2h += 8 * a.n_rows + 8 * lo.n_rows
 
     # The chains (inspect(A) + spmv and inspect(L) + sptrsv of each matrix)
@@ -795,15 +791,10 @@ def run_e2e(args, D, ddf, torch, dev, stream, exec_b, world):
     # only for its own arrays: the long solve chains start while the remaining
     # arrays are still being copied, instead of after all of them.
     opts_L = ddf.ddf_opts_default(coarsen_rows=args.coarsen) if args.coarsen is not None else None
-    opts_in_a = ddf.ddf_opts_default(lower_of_input=1)
-    if args.coarsen is not None:
-        opts_in_a.coarsen_rows = args.coarsen
     copy = torch.cuda.Stream(device=dev)
     size = lambda i: D[i]["a"].nnz + D[i]["lo"].nnz  # noqa: E731
     by_size = sorted(range(len(D)), key=lambda i: -size(i))
     order = [("L", i) for i in by_size] + [("A", i) for i in by_size]
-    # matrices whose L is read inside A: one upload of A serves both chains
-    shared_a = {i for i in range(len(D)) if H[i]["L"] is None}
     lo_p, hi_p = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
     streams = {job: torch.cuda.Stream(device=dev, priority=hi_p if job[1] == by_size[0] else lo_p)
                for job in order}
@@ -824,8 +815,7 @@ def run_e2e(args, D, ddf, torch, dev, stream, exec_b, world):
                 ddf.ddf_spmv(p, g[3], out, stream=s)
                 h["y"].copy_(out, non_blocking=True)
             else:
-                p = ddf.ddf_inspect(*g[:3], d["lo"].n_cols, ddf.DDF_SPTRSV,
-                                    opts_in_a if i in shared_a else opts_L, s)
+                p = ddf.ddf_inspect(*g[:3], d["lo"].n_cols, ddf.DDF_SPTRSV, opts_L, s)
                 out = torch.empty(d["lo"].n_rows, dtype=torch.float64, device=dev)
                 ddf.ddf_sptrsv(p, g[3], out, stream=s)
                 h["xs"].copy_(out, non_blocking=True)
@@ -836,18 +826,11 @@ def run_e2e(args, D, ddf, torch, dev, stream, exec_b, world):
         for s in streams.values():
             s.wait_stream(stream)
         jobs = []
-        a_dev = {}
         with torch.cuda.stream(copy):
             for kind, i in order:
                 h = H[i]
-                if i in shared_a:
-                    # A once (the L chain's turn comes first), then each chain's vector
-                    if i not in a_dev:
-                        a_dev[i] = upload(h["A"])
-                    g = a_dev[i] + ((h["x"] if kind == "A" else h["b"]).to(dev, non_blocking=True),)
-                else:
-                    g = upload(h["A"]) + (h["x"].to(dev, non_blocking=True),) if kind == "A" else \
-                        upload(h["L"]) + (h["b"].to(dev, non_blocking=True),)
+                g = upload(h["A"]) + (h["x"].to(dev, non_blocking=True),) if kind == "A" else \
+                    upload(h["L"]) + (h["b"].to(dev, non_blocking=True),)
                 ev = torch.cuda.Event()
                 ev.record(copy)
                 jobs.append((kind, i, g, ev))
@@ -873,9 +856,7 @@ def run_e2e(args, D, ddf, torch, dev, stream, exec_b, world):
         times.append(e0.elapsed_time(e1))
     ms, v = aggregate(float(np.mean(times)), exec_b, world, dev)
     return {"value": round(v, 2), "unit": "GB/s",
-            "ms_per_step": round(ms, 3), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "sptrsv_input": {D[i]["name"]: ("lower triangle read inside A (lower_of_input)" if i in shared_a
-                                            else "L copied separately") for i in range(len(D))}}
+            "ms_per_step": round(ms, 3), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
 
 # ---------------------------------------------------------------------------

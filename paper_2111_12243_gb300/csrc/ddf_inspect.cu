@@ -117,7 +117,7 @@ __global__ void k_i64_to_i32(const int64_t* __restrict__ in, int32_t* __restrict
 // findDependencies: level[i] = 1 + max level of its off-diagonal columns
 // ---------------------------------------------------------------------------
 constexpr int LEV_CHUNK = 1024;                               // rows per CTA ticket (a multiple of 1024)
-constexpr int LEV_MAXSEG = 128;                               // longest run one warp takes at once
+constexpr int LEV_MAXSEG = 256;                               // longest run one warp takes at once
 
 // Bounded wait on a level written by another CTA: a few immediate polls, then
 // exponential backoff so that waiting warps do not flood L2 with requests.

@@ -247,27 +247,51 @@ k_spmv_tile(const dcod* __restrict__ cod, const dtile* __restrict__ tiles, int64
 // point and no shuffle reduction; a row's sum runs in point order.  Units of
 // more than PSC2_STAGE points (one row each, since a unit closes before a row
 // that would take it past unit_nnz) run the row with all 32 lanes and one
-// shuffle reduction; rows of more than DDF_LONG_ROW points are left to
-// k_spmv_long.
+// shuffle reduction.  Rows of more than DDF_LONG_ROW points run one CTA per
+// row: the first nlong CTAs of the launch take one such row each (threads
+// over the row's points, then a reduction in a fixed order: shuffles inside
+// each warp, warps in index order, so the result does not depend on
+// scheduling), and the other CTAs walk the units, skipping those rows.
 constexpr int PSC2_STAGE = 256;   // points of one unit staged in shared memory
 
 template <typename TV, typename TX, typename TY, typename TA>
 __global__ void __launch_bounds__(DDF_CTA_THREADS, SPMV_MIN_CTAS)
 k_spmv_psc2(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64_t nunits,
-            const int32_t* __restrict__ st, const int32_t* __restrict__ col, const TV* __restrict__ val,
-            const TX* __restrict__ x, TY* __restrict__ y) {
+            const int32_t* __restrict__ long_q, int64_t nlong, const int32_t* __restrict__ st,
+            const int32_t* __restrict__ col, const TV* __restrict__ val, const TX* __restrict__ x,
+            TY* __restrict__ y) {
     __shared__ TA prod_all[DDF_WARPS_PER_CTA][PSC2_STAGE];
     const int lane = threadIdx.x & 31;
+    if ((int64_t)blockIdx.x < nlong) {
+        TA* part = prod_all[0];
+        const int32_t q = long_q[blockIdx.x];
+        const int32_t a = st[q], b = st[q + 1];
+        TA acc = 0;
+#pragma unroll 4
+        for (int32_t k = a + (int32_t)threadIdx.x; k < b; k += DDF_CTA_THREADS)
+            acc += ddf_cvt<TA>(__ldcs(val + k)) * ddf_cvt<TA>(__ldg(x + __ldcs(col + k)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) part[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            TA t = 0;
+#pragma unroll
+            for (int w = 0; w < DDF_WARPS_PER_CTA; ++w) t += part[w];
+            y[q] = store_cvt<TY, TA>(t);   // SpMV positions are the rows
+        }
+        return;
+    }
     TA* prod = prod_all[threadIdx.x >> 5];
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nunits; u += nw) {
+    const int64_t nw = ((int64_t)(gridDim.x - nlong) * blockDim.x) >> 5;
+    for (int64_t u = (((int64_t)blockIdx.x - nlong) * blockDim.x + threadIdx.x) >> 5; u < nunits; u += nw) {
         const dunit U = units[u];
         const dcod C = cod[U.cod];
         const int32_t qa = C.q0 + U.i0b, qb = C.q0 + U.i0e;
         const int32_t ka = st[qa], kb = st[qb];
         const int32_t T = kb - ka;
         if (T > PSC2_STAGE) {
-            if (T > DDF_LONG_ROW) continue;   // one CTA per row (k_spmv_long)
+            if (T > DDF_LONG_ROW) continue;   // one of the CTAs above
             TA acc = 0;
 #pragma unroll 4
             for (int32_t k = ka + lane; k < kb; k += 32)
@@ -288,32 +312,6 @@ k_spmv_psc2(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64
             y[C.f0 + C.rho * (q - C.q0)] = store_cvt<TY, TA>(acc);
         }
         __syncwarp();
-    }
-}
-
-// PSC II rows of more than DDF_LONG_ROW points: one CTA per row, threads over
-// the row's points, then a reduction in a fixed order (shuffles inside each
-// warp, warps in index order), so the result does not depend on scheduling.
-template <typename TV, typename TX, typename TY, typename TA>
-__global__ void __launch_bounds__(DDF_CTA_THREADS)
-k_spmv_long(const int32_t* __restrict__ long_q, const int32_t* __restrict__ st, const int32_t* __restrict__ col,
-            const TV* __restrict__ val, const TX* __restrict__ x, TY* __restrict__ y) {
-    __shared__ TA part[DDF_WARPS_PER_CTA];
-    const int32_t q = long_q[blockIdx.x];
-    const int32_t a = st[q], b = st[q + 1];
-    TA acc = 0;
-#pragma unroll 4
-    for (int32_t k = a + (int32_t)threadIdx.x; k < b; k += DDF_CTA_THREADS)
-        acc += ddf_cvt<TA>(__ldcs(val + k)) * ddf_cvt<TA>(__ldg(x + __ldcs(col + k)));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        TA t = 0;
-#pragma unroll
-        for (int w = 0; w < DDF_WARPS_PER_CTA; ++w) t += part[w];
-        y[q] = store_cvt<TY, TA>(t);   // SpMV positions are the rows
     }
 }
 
@@ -355,15 +353,11 @@ int launch_all(ddf_plan_s* p, const TV* val, const TX* x, TY* y, cudaStream_t s)
         ddf_count_launch();
         ++launches;
     }
-    if (p->nlong > 0) {
-        k_spmv_long<TV, TX, TY, TA><<<(unsigned)p->nlong, DDF_CTA_THREADS, 0, s>>>(p->long_q, p->starts, p->col,
-                                                                               val, x, y);
-        ddf_count_launch();
-        ++launches;
-    }
     if (p->nunits[DDF_PSC2] > 0) {
-        k_spmv_psc2<TV, TX, TY, TA><<<grid_for(p->nunits[2], sm), DDF_CTA_THREADS, 0, s>>>(
-            p->cod, p->units[2], p->nunits[2], p->starts, p->col, val, x, y);
+        // the long rows' CTAs first, then those walking the units
+        const int64_t ctas = (int64_t)grid_for(p->nunits[2], sm) + p->nlong;
+        k_spmv_psc2<TV, TX, TY, TA><<<(unsigned)ctas, DDF_CTA_THREADS, 0, s>>>(
+            p->cod, p->units[2], p->nunits[2], p->long_q, p->nlong, p->starts, p->col, val, x, y);
         ddf_count_launch();
         ++launches;
     }
