@@ -530,9 +530,13 @@ def run_ours(args, rank, world, local_rank):
 
 
 # (dram__bytes_read.sum + dram__bytes_write.sum) / algorithmic bytes of one
-# launch, from one ncu capture of a smaller case of the same kernel (the
-# captures are summarised under profiles/).
-TRAFFIC_RATIO = {}
+# call, from one ncu capture of a smaller case of the same kernels (the
+# 27-point stencil at 126^3; the captures are summarised under profiles/).
+# The traffic grows with the rows processed, so the ratio carries over.
+TRAFFIC_RATIO = {
+    "ddf_sptrsv[st27_168]": (297527552 + 14641664) / 280366928,
+    "ddf_spmv[st27_168]": (460305152 + 4723456) / 463476904,
+}
 
 
 def chain_hop(ddf, torch, dev, stream, n_chain=8192, reps=5):

@@ -240,19 +240,27 @@ k_spmv_tile(const dcod* __restrict__ cod, const dtile* __restrict__ tiles, int64
     }
 }
 
-// PSC II units (whole consecutive rows, at most unit_nnz points): the warp
-// first forms the products val[k] * x[col[k]] of all the unit's points, lanes
-// over consecutive points (coalesced values and columns), into shared memory;
-// then each lane adds up whole rows from there.  One multiply and one add per
-// point and no shuffle reduction; a row's sum runs in point order.  Units of
+// PSC II units (whole consecutive rows, at most unit_nnz points).  Lane l
+// takes the unit's points [l K, (l + 1) K), K = ceil(points / 32), and adds
+// their products with fused multiply-adds in point order, row by row: a row
+// that starts and ends inside the lane's stretch is written at once.  A row
+// that crosses stretch boundaries has a partial sum in each lane it touches;
+// a 5-step scan over the lanes carries each lane's last partial into the
+// lanes that continue the same row, and the lane where the row ends writes
+// it.  About K + 7 FP64 warp instructions per unit (K fused multiply-adds, the
+// scan's adds), and no lane waits on a long row while the others idle.  The
+// unit's row starts are staged in shared memory for the lanes to find their
+// rows.  Empty rows are written 0 by a separate pass over the rows.  Units of
 // more than PSC2_STAGE points (one row each, since a unit closes before a row
 // that would take it past unit_nnz) run the row with all 32 lanes and one
-// shuffle reduction.  Rows of more than DDF_LONG_ROW points run one CTA per
+// shuffle reduction; rows of more than DDF_LONG_ROW points run one CTA per
 // row: the first nlong CTAs of the launch take one such row each (threads
 // over the row's points, then a reduction in a fixed order: shuffles inside
-// each warp, warps in index order, so the result does not depend on
-// scheduling), and the other CTAs walk the units, skipping those rows.
-constexpr int PSC2_STAGE = 256;   // points of one unit staged in shared memory
+// each warp, warps in index order), and the other CTAs walk the units,
+// skipping those rows.  Every sum has a fixed order, so results do not
+// depend on scheduling.
+constexpr int PSC2_STAGE = 256;   // most points of a unit run by the lane stretches
+constexpr int PSC2_ROWS = 256;    // rows of a unit (the unit builder's limit)
 
 template <typename TV, typename TX, typename TY, typename TA>
 __global__ void __launch_bounds__(DDF_CTA_THREADS, SPMV_MIN_CTAS)
@@ -260,10 +268,10 @@ k_spmv_psc2(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64
             const int32_t* __restrict__ long_q, int64_t nlong, const int32_t* __restrict__ st,
             const int32_t* __restrict__ col, const TV* __restrict__ val, const TX* __restrict__ x,
             TY* __restrict__ y) {
-    __shared__ TA prod_all[DDF_WARPS_PER_CTA][PSC2_STAGE];
+    __shared__ int32_t srow_all[DDF_WARPS_PER_CTA][PSC2_ROWS + 1];
+    __shared__ TA part[DDF_WARPS_PER_CTA];
     const int lane = threadIdx.x & 31;
     if ((int64_t)blockIdx.x < nlong) {
-        TA* part = prod_all[0];
         const int32_t q = long_q[blockIdx.x];
         const int32_t a = st[q], b = st[q + 1];
         TA acc = 0;
@@ -282,7 +290,7 @@ k_spmv_psc2(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64
         }
         return;
     }
-    TA* prod = prod_all[threadIdx.x >> 5];
+    int32_t* srow = srow_all[threadIdx.x >> 5];
     const int64_t nw = ((int64_t)(gridDim.x - nlong) * blockDim.x) >> 5;
     for (int64_t u = (((int64_t)blockIdx.x - nlong) * blockDim.x + threadIdx.x) >> 5; u < nunits; u += nw) {
         const dunit U = units[u];
@@ -290,6 +298,7 @@ k_spmv_psc2(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64
         const int32_t qa = C.q0 + U.i0b, qb = C.q0 + U.i0e;
         const int32_t ka = st[qa], kb = st[qb];
         const int32_t T = kb - ka;
+        const int32_t fb = C.f0 + C.rho * U.i0b;   // y index of the unit's first row
         if (T > PSC2_STAGE) {
             if (T > DDF_LONG_ROW) continue;   // one of the CTAs above
             TA acc = 0;
@@ -298,18 +307,69 @@ k_spmv_psc2(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64
                 acc += ddf_cvt<TA>(__ldcs(val + k)) * ddf_cvt<TA>(__ldg(x + __ldcs(col + k)));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) y[C.f0 + C.rho * U.i0b] = store_cvt<TY, TA>(acc);
+            if (lane == 0) y[fb] = store_cvt<TY, TA>(acc);
             continue;
         }
-#pragma unroll 4
-        for (int32_t e = lane; e < T; e += 32)
-            prod[e] = ddf_cvt<TA>(__ldcs(val + ka + e)) * ddf_cvt<TA>(__ldg(x + __ldcs(col + ka + e)));
+        const int32_t R = qb - qa;
+        for (int32_t i = lane; i <= R; i += 32) srow[i] = st[qa + i] - ka;
         __syncwarp();
-        for (int32_t q = qa + lane; q < qb; q += 32) {
-            const int32_t a = st[q] - ka, b = st[q + 1] - ka;
+        // empty rows
+        for (int32_t i = lane; i < R; i += 32)
+            if (srow[i + 1] == srow[i]) y[fb + C.rho * i] = store_cvt<TY, TA>((TA)0);
+        const int32_t K = (T + 31) >> 5;
+        const int32_t e0 = min(lane * K, T), e1 = min(e0 + K, T);
+        TA hp = 0, tp = 0;
+        int32_t hr = 0, tr = 0;
+        bool cont = false, single = true;
+        if (e0 < e1) {
+            // the row holding point e0: the last row starting at or before it
+            int32_t lo = 0, hi = R - 1;
+            while (lo < hi) {
+                const int32_t mid = (lo + hi + 1) >> 1;
+                if (srow[mid] <= e0) lo = mid;
+                else hi = mid - 1;
+            }
+            int32_t r = lo;
+            hr = r;
+            cont = srow[r] < e0;
             TA acc = 0;
-            for (int32_t k = a; k < b; ++k) acc += prod[k];
-            y[C.f0 + C.rho * (q - C.q0)] = store_cvt<TY, TA>(acc);
+            int32_t next = srow[r + 1];
+            for (int32_t e = e0; e < e1; ++e) {
+                while (next <= e) {   // row r ended before point e
+                    if (single) hp = acc;
+                    else if (next > srow[r]) y[fb + C.rho * r] = store_cvt<TY, TA>(acc);   // inside the stretch
+                    single = false;
+                    acc = 0;
+                    ++r;
+                    next = srow[r + 1];
+                }
+                acc += ddf_cvt<TA>(__ldcs(val + ka + e)) * ddf_cvt<TA>(__ldg(x + __ldcs(col + ka + e)));
+            }
+            tr = r;
+            tp = acc;
+            if (single) hp = acc;
+        }
+        // carry_out(l) = tp(l) + [single(l) and cont(l)] carry_out(l - 1): a scan over the lanes
+        TA cb = tp;
+        bool ca = single && cont && e0 < e1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const TA pb = __shfl_up_sync(0xffffffffu, cb, o);
+            const bool pa = __shfl_up_sync(0xffffffffu, ca, o);
+            if (lane >= o) {
+                if (ca) cb += pb;
+                ca = ca && pa;
+            }
+        }
+        const TA prev = __shfl_up_sync(0xffffffffu, cb, 1);
+        const TA cin = (lane > 0 && cont) ? prev : (TA)0;
+        if (e0 < e1) {
+            if (!single) {
+                y[fb + C.rho * hr] = store_cvt<TY, TA>(hp + cin);   // the head row ended in the stretch
+                if (srow[tr + 1] == e1) y[fb + C.rho * tr] = store_cvt<TY, TA>(tp);
+            } else if (srow[hr + 1] == e1) {
+                y[fb + C.rho * hr] = store_cvt<TY, TA>(hp + cin);
+            }
         }
         __syncwarp();
     }
