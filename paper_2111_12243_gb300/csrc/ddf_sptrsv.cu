@@ -244,9 +244,11 @@ k_sptrsv(const dcod* __restrict__ cod, const dunit* __restrict__ units, const in
         solve_ld1(units, unit_q, u + 3 * nw, nunits, t3);
         // While some dependencies held in registers are not ready, every lane
         // re-reads its own missing values, so one round trip checks all of
-        // the warp's late dependencies at once.  The wait is bounded: every
-        // 16 rounds the warp checks the abort flag and the time since it
-        // started waiting, and past cap_ns it latches DDF_ERR_TIMEOUT.
+        // the warp's late dependencies at once; the next round is issued as
+        // soon as the last returns (a pause between rounds measured slower).
+        // The wait is bounded: every 16 rounds the warp checks the abort flag
+        // and the time since it started waiting, and past cap_ns it latches
+        // DDF_ERR_TIMEOUT.
         uint64_t tw = 0;
         uint32_t rounds = 0;
         while (true) {
@@ -265,7 +267,6 @@ k_sptrsv(const dcod* __restrict__ cod, const dunit* __restrict__ units, const in
                 }
                 stop = late || __any_sync(0xffffffffu, ddf_ld_relaxed_s32(abort_flag) != 0);
             }
-            if (rounds > 64) __nanosleep(64);
 #pragma unroll
             for (int k = 0; k < SOLVE_SMAX; ++k)
                 if ((cur.li + k * cur.v < cur.L) && xv[k] == B::SENT)
