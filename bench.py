@@ -79,6 +79,10 @@ def parse(argv=None):
                     help="1: everything on one stream; 2: one stream and host thread per matrix; "
                          "4 (default): one per chain, inspect(A)+spmv and inspect(L)+sptrsv of each matrix")
     ap.add_argument("--serial", action="store_true", help="same as --streams 1")
+    ap.add_argument("--prio", default="chain", choices=["chain", "size"],
+                    help="stream priorities: 'chain' (default) gives the inspect(L) + sptrsv chains the high "
+                         "priority and the inspect(A) + spmv chains the low one; 'size' gives both chains of "
+                         "the largest matrix the high priority")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--coarsen", type=int, default=None,
                     help="SpTRSV rows per block (coarsen_rows; 0 = plain level sets; default: library default)")
@@ -312,13 +316,19 @@ def run_ours(args, rank, world, local_rank):
         chain_a(d, s, e, rec, out, i)
         chain_l(d, s, e, rec, out, i)
 
-    # Larger matrices have the longer pipelines: their streams get the higher
-    # priority, the others fill the SMs they leave idle.
+    # The inspect(L) + sptrsv chains are the longer, latency-bound pipelines:
+    # by default their streams get the higher priority and the bandwidth-bound
+    # inspect(A) + spmv chains fill the SMs they leave idle ('--prio size':
+    # both chains of the largest matrix high, the others low).
     order = sorted(range(len(D)), key=lambda i: -(D[i]["a"].nnz + D[i]["lo"].nnz))
     lo_p, hi_p = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
-    prio = {i: (hi_p if k == 0 else lo_p) for k, i in enumerate(order)}
-    side = [torch.cuda.Stream(device=dev, priority=prio[i]) for i in range(len(D))]
-    side_l = [torch.cuda.Stream(device=dev, priority=prio[i]) for i in range(len(D))]
+    if args.prio == "chain":
+        prio_a = {i: lo_p for i in range(len(D))}
+        prio_l = {i: hi_p for i in range(len(D))}
+    else:
+        prio_a = prio_l = {i: (hi_p if k == 0 else lo_p) for k, i in enumerate(order)}
+    side = [torch.cuda.Stream(device=dev, priority=prio_a[i]) for i in range(len(D))]
+    side_l = [torch.cuda.Stream(device=dev, priority=prio_l[i]) for i in range(len(D))]
 
     def step(record):
         """One step; returns per-matrix phase events, plan stats and the step's
@@ -654,6 +664,8 @@ def run_batch(args, ddf, torch, dev, stream, flush, nrhs=32, reps=5):
     for p in pa + pl + pa64 + pl64 + [pA, pL]:
         p.destroy()
     return {"matrices": len(mats), "rows": int(N), "nnz": int(nnzA), "nnz_lower": int(nnzL), "nrhs": nrhs,
+            "sptrsm_levels": sl["levels"],
+            "sptrsm_us_per_level": round(t_trsm * 1e3 / max(sl["levels"], 1), 3),
             "dtype": "f32 values and vectors, f32 sums", "tile_spmm_unit_nnz": tile_spmv,
             "tile_sptrsm_units_per_cta": tile_trsv, "graph_ms": round(t_graph, 4), "graph_status": st_graph,
             "graph_gbs": round((bytes_spmm + bytes_trsm) / (t_graph * 1e-3) / 1e9, 1),
@@ -1008,6 +1020,8 @@ def main(argv=None):
                        "step": "inspect(A)+spmv+inspect(L)+sptrsv per matrix",
                        "l2": "256 MB written then another 256 MB read between steps (the flush's "
                              "write-back happens before the timed work); inputs larger than L2",
+                       "priorities": {"chain": "inspect(L)+sptrsv chains high, inspect(A)+spmv chains low",
+                                      "size": "both chains of the largest matrix high"}[args.prio],
                        "streams": {1: "everything on one stream",
                                    2: "one stream and host thread per matrix",
                                    4: "one stream and host thread per chain: inspect(A)+spmv, "

@@ -240,27 +240,36 @@ DDF_API ddf_status ddf_inspect_batch(const ddf_csr* mats, int32_t count, ddf_kin
  * Multi-RHS SpMV: Y = A X for nrhs (1..32) right-hand sides.  X is
  * [n_cols][nrhs] and Y [n_rows][nrhs], row-major, device memory, of dtype
  * DDF_F64 (FP64 values and sums) or DDF_F32 (the plan's FP32 values, FP32
- * sums; the plan needs store_dtype DDF_F32).  One warp runs one row at a
- * time, lane k accumulating right-hand side k, so no reduction is needed.
+ * sums; the plan needs store_dtype DDF_F32).  Runs the SpMV plan's codelets
+ * (Sec. III-B) with one warp per matrix row at a time.  When nrhs is 16 bytes
+ * times a power of two from 2 to 16 (FP32: 8, 16, 32; FP64: 4, 8, 16, 32)
+ * and X and Y start on 16-byte boundaries, a lane moves 16 bytes of a row of
+ * X and one load of the warp fetches the X rows of several points; otherwise
+ * lane k owns right-hand side k.  Either way the summation order is fixed.
  */
 DDF_API ddf_status ddf_spmm(ddf_plan_t p, const void* X, void* Y, int32_t nrhs, ddf_dtype dtype, ddf_stream_t s);
 
 /*
  * Multi-RHS SpTRSV: solves L X = B for nrhs (1..32) right-hand sides, layouts
- * and dtypes as in ddf_spmm (B and X must not overlap).  Same level-ordered
- * codelets and per-element ready flags as ddf_sptrsv; the work of one
- * dependency hop is nrhs rows of work instead of one.  Plain launches only
- * (no cooperative launch), so the call can be recorded in a CUDA graph.
+ * and dtypes as in ddf_spmm (B and X must not overlap).  Rows run in the
+ * plan's level order (the partitions of Sec. IV-A) with per-element ready
+ * flags as in ddf_sptrsv, one warp per row at a time, lanes laid out as in
+ * ddf_spmm; each warp of a persistent grid takes the next work units (rows
+ * of one level) from a ticket.
+ * Plain launches only (no cooperative launch), so the call can be recorded
+ * in a CUDA graph.
  */
 DDF_API ddf_status ddf_sptrsm(ddf_plan_t p, const void* B, void* X, int32_t nrhs, ddf_dtype dtype,
                               ddf_stream_t s);
 
 /*
- * Autotuner for the multi-RHS executors: rebuilds the plan's work units for
- * each candidate tile size (target nonzeros per unit), times ddf_spmm (kind
- * DDF_SPMV) or ddf_sptrsm (DDF_SPTRSV) on the given operands with CUDA events,
- * and keeps the fastest.  *best_unit_nnz receives the choice (may be NULL).
- * Overwrites the output operand.  Synchronises s.
+ * Autotuner for the multi-RHS executors.  Kind DDF_SPMV: rebuilds the plan's
+ * work units for each candidate tile size (target nonzeros per unit: 64 ..
+ * 2048) and times ddf_spmm; kind DDF_SPTRSV: times ddf_sptrsm for each
+ * candidate number of work units a warp takes per ticket (1 .. 8).  Timing uses CUDA
+ * events on the given operands; the fastest candidate is kept and returned
+ * in *best_unit_nnz (may be NULL).  Overwrites the output operand.
+ * Synchronises s.
  */
 DDF_API ddf_status ddf_tune(ddf_plan_t p, const void* in, void* out, int32_t nrhs, ddf_dtype dtype,
                             ddf_stream_t s, int32_t* best_unit_nnz);

@@ -4,12 +4,16 @@
 // its partitions and codelets are those of Alg. 1 on that matrix, so every
 // level of a batched SpTRSV holds the rows of all matrices at that level.
 //
-// The multi-RHS executors run the same codelets with a different lane map:
-// one warp runs one row at a time and lane k owns right-hand side k, so
-// every lane does one multiply-add per point and no reduction is needed.
-// A row's points are read 32 at a time (lane t loads point t's value and
-// column) and broadcast with shuffles; the right-hand sides of one column are
-// contiguous, so a warp reads them with one coalesced access.
+// The multi-RHS executors give a row of the block X ([n][nrhs], row-major)
+// to a group of LP lanes: each lane moves VEC consecutive right-hand sides
+// (16 bytes when nrhs = VEC * LP and the blocks are 16-byte aligned, else
+// one element, LP = 32, lane k owning right-hand side k).  A warp runs one
+// matrix row at a time: its G = 32 / LP lane groups take G different points
+// of the row, so one load instruction fetches the X rows of G points, and
+// group g sums the points t = g (mod G).  The G partial sums are combined by
+// a butterfly over the groups, a fixed order, so results do not depend on
+// timing.  A row's points (value, column) are read 32 at a time, lane t
+// loading point t, and handed to the groups with shuffles.
 #include <vector>
 
 #include "ddf_internal.cuh"
@@ -23,6 +27,8 @@ __global__ void k_add_offset(int32_t* __restrict__ a, int64_t n, int32_t add) {
         a[i] += add;
 }
 
+// Bits of one element of X: the fill pattern that marks "not solved yet" and
+// the canonical NaN a solved element takes if its bits equal the pattern.
 template <typename TX>
 struct RB;
 template <>
@@ -43,8 +49,82 @@ struct RB<float> {
     static __device__ __forceinline__ U ld(const void* p) { return ddf_ld_relaxed_u32(p); }
     static __device__ __forceinline__ void st(void* p, U v) { ddf_st_relaxed_u32(p, v); }
     static __device__ __forceinline__ float val(U v) { return __uint_as_float(v); }
-    static __device__ __forceinline__ U bits(float v) { return __float_as_uint(v); }
+    static __device__ __forceinline__ U bits(float v) { return (U)__float_as_uint(v); }
 };
+
+// Access to VEC consecutive right-hand sides of one row of X: plain reads
+// (SpMM), relaxed reads and writes of the ready-flag protocol (SpTRSM).
+template <typename TX, int VEC>
+struct VA;
+template <typename TX>
+struct VA<TX, 1> {
+    using U = typename RB<TX>::U;
+    static __device__ __forceinline__ void ld_nc(const TX* p, TX (&o)[1]) { o[0] = __ldg(p); }
+    static __device__ __forceinline__ void st(TX* p, const TX (&v)[1]) { *p = v[0]; }
+    static __device__ __forceinline__ void ld_relaxed(const void* p, U (&o)[1]) { o[0] = RB<TX>::ld(p); }
+    static __device__ __forceinline__ void st_relaxed(void* p, const U (&v)[1]) { RB<TX>::st(p, v[0]); }
+};
+template <>
+struct VA<float, 4> {
+    using U = uint32_t;
+    static __device__ __forceinline__ void ld_nc(const float* p, float (&o)[4]) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+        o[0] = t.x;
+        o[1] = t.y;
+        o[2] = t.z;
+        o[3] = t.w;
+    }
+    static __device__ __forceinline__ void st(float* p, const float (&v)[4]) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    static __device__ __forceinline__ void ld_relaxed(const void* p, U (&o)[4]) {
+        asm volatile("ld.relaxed.gpu.global.v4.b32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3])
+                     : "l"(p)
+                     : "memory");
+    }
+    static __device__ __forceinline__ void st_relaxed(void* p, const U (&v)[4]) {
+        asm volatile("st.relaxed.gpu.global.v4.b32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v[0]), "r"(v[1]),
+                     "r"(v[2]), "r"(v[3])
+                     : "memory");
+    }
+};
+template <>
+struct VA<double, 2> {
+    using U = unsigned long long;
+    static __device__ __forceinline__ void ld_nc(const double* p, double (&o)[2]) {
+        const double2 t = __ldg(reinterpret_cast<const double2*>(p));
+        o[0] = t.x;
+        o[1] = t.y;
+    }
+    static __device__ __forceinline__ void st(double* p, const double (&v)[2]) {
+        *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    }
+    static __device__ __forceinline__ void ld_relaxed(const void* p, U (&o)[2]) {
+        asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(o[0]), "=l"(o[1]) : "l"(p) : "memory");
+    }
+    static __device__ __forceinline__ void st_relaxed(void* p, const U (&v)[2]) {
+        asm volatile("st.relaxed.gpu.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(v[0]), "l"(v[1]) : "memory");
+    }
+};
+
+// Lane layout of the executors: VEC elements per lane, LP lanes per row of
+// X, G groups per warp, NL loads per lane in flight together, SUB points
+// covered by them.
+template <typename TX, int VEC_, int LP_>
+struct Lay {
+    static constexpr int VEC = VEC_, LP = LP_, G = 32 / LP_, NL = LP_ < 8 ? LP_ : 8, SUB = NL * (32 / LP_);
+    using V = VA<TX, VEC_>;
+};
+
+// sum over the G lane groups; afterwards every group holds the row's total
+template <typename TX, int LP, int VEC>
+__device__ __forceinline__ void group_sum(TX (&acc)[VEC]) {
+#pragma unroll
+    for (int off = LP; off < 32; off <<= 1)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
+}
 
 // Column of point i1 of row i0 of codelet C (the three access functions of h).
 __device__ __forceinline__ int32_t point_col(const dcod& C, const int32_t* __restrict__ col, int32_t i0,
@@ -55,84 +135,266 @@ __device__ __forceinline__ int32_t point_col(const dcod& C, const int32_t* __res
     return col[kb + i1];
 }
 
-// y_r[k] = sum over the row's points of a * x_col[k], k = lane < nrhs.
-// Point i1's value is val[kb + i1 * vs] (vs > 1 for rows of SpMV value tiles).
+// ---------------------------------------------------------------------------
+// SpMM: Y = A X over the SpMV plan's work units and value tiles
+// ---------------------------------------------------------------------------
+
+// A row of the multi-RHS SpMV: its first 32 points (lane t: point t's value
+// and column), its value extent, and the row of Y it writes.  Point i1's value
+// is val[kb + i1 * vs] (vs > 1 for rows of SpMV value tiles).
+template <typename TX>
+struct SRow {
+    int32_t kb, L, vs, pj, f;
+    TX pv;
+};
+
 template <typename TV, typename TX>
-__device__ __forceinline__ TX row_mrhs(const dcod& C, int32_t i0, const int32_t* __restrict__ st,
-                                      const int32_t* __restrict__ col, const TV* __restrict__ val,
-                                      const TX* __restrict__ X, int32_t nrhs, int lane, int32_t vs = 1,
-                                      int32_t vb = -1) {
+__device__ __forceinline__ void srow_point(const dcod& C, int32_t i0, int32_t kb, int32_t L, int32_t vs,
+                                           int32_t i1, const int32_t* __restrict__ col,
+                                           const TV* __restrict__ val, TX& pv, int32_t& pj) {
+    pv = (TX)0;
+    pj = 0;
+    if (i1 < L) {
+        pv = ddf_cvt<TX>(__ldcs(val + kb + (int64_t)i1 * vs));
+        pj = point_col(C, col, i0, kb, i1);
+    }
+}
+
+template <typename TV, typename TX>
+__device__ __forceinline__ void srow_load(const dcod& C, int32_t i0, bool act, const int32_t* __restrict__ st,
+                                          const int32_t* __restrict__ col, const TV* __restrict__ val, int lane,
+                                          int32_t vs, int32_t vb, SRow<TX>& m) {
+    m.kb = m.L = m.pj = m.f = 0;
+    m.vs = vs;
+    m.pv = (TX)0;
+    if (!act) return;
     const int32_t q = C.q0 + i0;
-    int32_t kb, L;
     if (C.type == DDF_PSC2) {
+        m.kb = st[q];
+        m.L = st[q + 1] - m.kb;
+    } else {
+        m.kb = vb >= 0 ? vb : C.g0 + C.gamma * i0;
+        m.L = C.n;
+    }
+    m.f = C.f0 + C.rho * i0;
+    srow_point<TV, TX>(C, i0, m.kb, m.L, vs, lane, col, val, m.pv, m.pj);
+}
+
+// y_r = sum over the row's points of a * x_col
+template <typename TV, typename TX, class LY>
+__device__ __forceinline__ void srow_compute(const dcod& C, int32_t i0, const SRow<TX>& m,
+                                             const int32_t* __restrict__ col, const TV* __restrict__ val,
+                                             const TX* __restrict__ X, TX* __restrict__ Y, int32_t nrhs, int lane) {
+    using V = typename LY::V;
+    constexpr int VEC = LY::VEC, G = LY::G, NL = LY::NL, SUB = LY::SUB;
+    const int g = lane / LY::LP, c = lane % LY::LP;
+    const bool on = c * VEC < nrhs;
+    TX acc[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[v] = (TX)0;
+    TX pv = m.pv;
+    int32_t pj = m.pj;
+    for (int32_t p0 = 0; p0 < m.L; p0 += 32) {
+        TX npv = (TX)0;
+        int32_t npj = 0;
+        if (p0 + 32 < m.L) srow_point<TV, TX>(C, i0, m.kb, m.L, m.vs, p0 + 32 + lane, col, val, npv, npj);
+        const int32_t cnt = min(32, m.L - p0);
+        for (int32_t s0 = 0; s0 < cnt; s0 += SUB) {
+            TX xv[NL][VEC];
+            TX av[NL];
+#pragma unroll
+            for (int k = 0; k < NL; ++k) {
+                const int t = s0 + k * G + g;
+                av[k] = __shfl_sync(0xffffffffu, pv, t & 31);
+                const int32_t j = __shfl_sync(0xffffffffu, pj, t & 31);
+                if (on && t < cnt) {
+                    V::ld_nc(X + (int64_t)j * nrhs + c * VEC, xv[k]);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) xv[k][v] = (TX)0;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NL; ++k)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[v] += av[k] * xv[k][v];
+        }
+        pv = npv;
+        pj = npj;
+    }
+    group_sum<TX, LY::LP, VEC>(acc);
+    if (g == 0 && on) V::st(Y + (int64_t)m.f * nrhs + c * VEC, acc);
+}
+
+// A row of at most SHORT_ROW points on one lane group (group g of LP lanes):
+// the group walks the row's points NB at a time, lane c < NB loading point
+// p0 + c's value and column, every lane reading its VEC right-hand sides of
+// each point's X row; the group writes its row of Y.  The group's shuffles
+// name only its own lanes.
+constexpr int SHORT_ROW = 32;
+
+template <typename TV, typename TX, class LY>
+__device__ __forceinline__ void gspmm_row(const dcod& C, int32_t i0, int32_t kb, int32_t L, int32_t vs, int32_t f,
+                                          const int32_t* __restrict__ col, const TV* __restrict__ val,
+                                          const TX* __restrict__ X, TX* __restrict__ Y, int32_t nrhs, int g,
+                                          int c) {
+    using V = typename LY::V;
+    constexpr int VEC = LY::VEC, LP = LY::LP, NB = LY::NL;
+    const unsigned gmask = ((1u << LP) - 1u) << (g * LP);
+    TX acc[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[v] = (TX)0;
+    for (int32_t p0 = 0; p0 < L; p0 += NB) {
+        TX pv = (TX)0;
+        int32_t pj = 0;
+        if (c < NB && p0 + c < L) {
+            pv = ddf_cvt<TX>(__ldcs(val + kb + (int64_t)(p0 + c) * vs));
+            pj = point_col(C, col, i0, kb, p0 + c);
+        }
+        const int32_t cnt = min(NB, L - p0);
+        TX xv[NB][VEC];
+        TX av[NB];
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+            av[t] = __shfl_sync(gmask, pv, t, LP);
+            const int32_t j = __shfl_sync(gmask, pj, t, LP);
+            if (t < cnt) {
+                V::ld_nc(X + (int64_t)j * nrhs + c * VEC, xv[t]);
+            } else {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) xv[t][v] = (TX)0;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < NB; ++t)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[v] += av[t] * xv[t][v];
+    }
+    V::st(Y + (int64_t)f * nrhs + c * VEC, acc);
+}
+
+// Value extent of row i0 of codelet C (vb >= 0: a tile row, values at vb + i1 vs).
+__device__ __forceinline__ void spmm_row_extent(const dcod& C, int32_t i0, int32_t vb,
+                                                const int32_t* __restrict__ st, int32_t& kb, int32_t& L) {
+    if (C.type == DDF_PSC2) {
+        const int32_t q = C.q0 + i0;
         kb = st[q];
         L = st[q + 1] - kb;
     } else {
         kb = vb >= 0 ? vb : C.g0 + C.gamma * i0;
         L = C.n;
     }
-    TX acc = 0;
-    for (int32_t p0 = 0; p0 < L; p0 += 32) {
-        const int32_t i1 = p0 + lane;
-        TX pv = 0;
-        int32_t pj = 0;
-        if (i1 < L) {
-            pv = ddf_cvt<TX>(__ldcs(val + kb + (int64_t)i1 * vs));
-            pj = point_col(C, col, i0, kb, i1);
-        }
-        const int32_t cnt = min(32, L - p0);
-#pragma unroll 8
-        for (int32_t t = 0; t < cnt; ++t) {
-            const TX a = __shfl_sync(0xffffffffu, pv, t);
-            const int32_t j = __shfl_sync(0xffffffffu, pj, t);
-            if (lane < nrhs) acc += a * __ldg(X + (int64_t)j * nrhs + lane);
-        }
-    }
-    return acc;
 }
 
-template <typename TV, typename TX>
+// One warp per work unit.  Element-per-lane layout: rows in pairs, the next
+// row's points loading while the current row's X rows are read.  16-byte
+// layout: G rows at a time, one per lane group when all have at most
+// SHORT_ROW points, else one after another on the whole warp.
+template <typename TV, typename TX, class LY>
 __global__ void __launch_bounds__(DDF_CTA_THREADS)
 k_spmm(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64_t nunits,
        const int32_t* __restrict__ st, const int32_t* __restrict__ col, const TV* __restrict__ val,
        const TX* __restrict__ X, TX* __restrict__ Y, int32_t nrhs) {
+    constexpr int G = LY::G, LP = LY::LP;
     const int lane = threadIdx.x & 31;
+    const int g = lane / LP, c = lane % LP;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nunits; u += nw) {
         const dunit U = units[u];
         const int32_t c0 = U.cod;
         const int32_t ncods = U.i0b < 0 ? -U.i0b : 1;
-        for (int32_t c = 0; c < ncods; ++c) {
-            const dcod C = cod[c0 + c];
+        for (int32_t k = 0; k < ncods; ++k) {
+            const dcod C = cod[c0 + k];
             const int32_t b0 = U.i0b < 0 ? 0 : U.i0b;
             const int32_t e0 = U.i0b < 0 ? C.m : U.i0e;
-            for (int32_t i0 = b0; i0 < e0; ++i0) {
-                const TX acc = row_mrhs<TV, TX>(C, i0, st, col, val, X, nrhs, lane);
-                if (lane < nrhs) Y[(int64_t)(C.f0 + C.rho * i0) * nrhs + lane] = acc;
+            if constexpr (LP == 32) {
+                SRow<TX> ma, mb;
+                srow_load<TV, TX>(C, b0, b0 < e0, st, col, val, lane, 1, -1, ma);
+                for (int32_t i0 = b0; i0 < e0; i0 += 2) {
+                    srow_load<TV, TX>(C, i0 + 1, i0 + 1 < e0, st, col, val, lane, 1, -1, mb);
+                    srow_compute<TV, TX, LY>(C, i0, ma, col, val, X, Y, nrhs, lane);
+                    if (i0 + 1 >= e0) break;
+                    srow_load<TV, TX>(C, i0 + 2, i0 + 2 < e0, st, col, val, lane, 1, -1, ma);
+                    srow_compute<TV, TX, LY>(C, i0 + 1, mb, col, val, X, Y, nrhs, lane);
+                }
+            } else {
+                for (int32_t i0 = b0; i0 < e0; i0 += G) {
+                    const int32_t i = i0 + g;
+                    int32_t kb = 0, L = 0;
+                    if (i < e0) spmm_row_extent(C, i, -1, st, kb, L);
+                    if (!__any_sync(0xffffffffu, L > SHORT_ROW)) {
+                        if (i < e0)
+                            gspmm_row<TV, TX, LY>(C, i, kb, L, 1, C.f0 + C.rho * i, col, val, X, Y, nrhs, g, c);
+                    } else {
+                        for (int32_t h = i0; h < min(i0 + G, e0); ++h) {
+                            SRow<TX> m;
+                            srow_load<TV, TX>(C, h, true, st, col, val, lane, 1, -1, m);
+                            srow_compute<TV, TX, LY>(C, h, m, col, val, X, Y, nrhs, lane);
+                        }
+                    }
+                }
             }
         }
     }
 }
 
-// Rows of SpMV value tiles (point-major values), one warp per tile.
-template <typename TV, typename TX>
+// Rows of SpMV value tiles (point-major values), one warp per tile, rows laid
+// out over the lanes as in k_spmm.
+template <typename TV, typename TX, class LY>
 __global__ void __launch_bounds__(DDF_CTA_THREADS)
 k_spmm_tile(const dcod* __restrict__ cod, const dtile* __restrict__ tiles, int64_t ntiles,
             const int32_t* __restrict__ st, const int32_t* __restrict__ col, const TV* __restrict__ val,
             const TX* __restrict__ X, TX* __restrict__ Y, int32_t nrhs) {
+    constexpr int G = LY::G, LP = LY::LP;
     const int lane = threadIdx.x & 31;
+    const int g = lane / LP, c = lane % LP;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles; t += nw) {
         const dtile T = tiles[t];
         const int32_t w = (int32_t)(T.meta & 7u) + 1;
-        for (int32_t r = 0; r < w; ++r) {
-            const dcod C = cod[T.cod + (int32_t)((T.meta >> (3 + 3 * r)) & 7u)];
-            const int32_t i0 = T.q + r - C.q0;
-            const TX acc = row_mrhs<TV, TX>(C, i0, st, col, val, X, nrhs, lane, w, T.vb + r);
-            if (lane < nrhs) Y[(int64_t)(C.f0 + C.rho * i0) * nrhs + lane] = acc;
+        auto codelet = [&](int32_t r) { return cod[T.cod + (int32_t)((T.meta >> (3 + 3 * r)) & 7u)]; };
+        if constexpr (LP == 32) {
+            SRow<TX> ma, mb;
+            dcod Ca = codelet(0), Cb = Ca;
+            srow_load<TV, TX>(Ca, T.q - Ca.q0, true, st, col, val, lane, w, T.vb, ma);
+            for (int32_t r = 0; r < w; r += 2) {
+                if (r + 1 < w) {
+                    Cb = codelet(r + 1);
+                    srow_load<TV, TX>(Cb, T.q + r + 1 - Cb.q0, true, st, col, val, lane, w, T.vb + r + 1, mb);
+                }
+                srow_compute<TV, TX, LY>(Ca, T.q + r - Ca.q0, ma, col, val, X, Y, nrhs, lane);
+                if (r + 1 >= w) break;
+                if (r + 2 < w) {
+                    Ca = codelet(r + 2);
+                    srow_load<TV, TX>(Ca, T.q + r + 2 - Ca.q0, true, st, col, val, lane, w, T.vb + r + 2, ma);
+                }
+                srow_compute<TV, TX, LY>(Cb, T.q + r + 1 - Cb.q0, mb, col, val, X, Y, nrhs, lane);
+            }
+        } else {
+            for (int32_t r0 = 0; r0 < w; r0 += G) {
+                const int32_t r = r0 + g;
+                dcod C = codelet(min(r, w - 1));
+                const int32_t i = T.q + r - C.q0;
+                const int32_t L = r < w ? C.n : 0;   // tile rows are BLAS / PSC I rows of C.n points
+                if (!__any_sync(0xffffffffu, L > SHORT_ROW)) {
+                    if (r < w)
+                        gspmm_row<TV, TX, LY>(C, i, T.vb + r, L, w, C.f0 + C.rho * i, col, val, X, Y, nrhs, g, c);
+                } else {
+                    for (int32_t h = r0; h < min(r0 + G, w); ++h) {
+                        const dcod Ch = codelet(h);
+                        SRow<TX> m;
+                        srow_load<TV, TX>(Ch, T.q + h - Ch.q0, true, st, col, val, lane, w, T.vb + h, m);
+                        srow_compute<TV, TX, LY>(Ch, T.q + h - Ch.q0, m, col, val, X, Y, nrhs, lane);
+                    }
+                }
+            }
         }
     }
 }
+
+// ---------------------------------------------------------------------------
+// SpTRSM: L X = B over the SpTRSV plan, one row per warp at a time
+// ---------------------------------------------------------------------------
 
 template <typename U>
 __global__ void k_fill_m(U* __restrict__ x, int64_t n, U pattern, uint32_t* __restrict__ ticket) {
@@ -168,87 +430,306 @@ __device__ __noinline__ TX wait_m(const TX* p, int32_t* status, uint32_t* abort_
     }
 }
 
-constexpr int SM_E = 8;   // points of a row whose loads are in flight together
+// What a row of the solve needs before its dependencies: its row r, value
+// extent, the lane's entries of b, 1 / L_rr, and lane t's point t (value and
+// column) of its first 32 points.  The plan keeps every position's
+// off-diagonal points in level order (starts, col, val), whatever the type of
+// the codelet holding it, so the solve reads rows without the codelets.
+template <typename TX, int VEC>
+struct QRow {
+    int32_t r, kb, L, pj;
+    TX di, pv;
+    TX bv[VEC];
+};
 
-// Multi-RHS forward substitution over the level-ordered plan.  Each CTA
-// takes the next chunk of upc work units from the ticket when it starts, so
-// every unit it waits on belongs to a CTA that already runs (no co-residency
-// needed, hence no cooperative launch).  Row x[r][k] is ready once it no
-// longer holds the fill pattern; lane k waits on its own element, and the
-// lanes of a warp read one row of X with one coalesced access.
-template <typename TV, typename TX>
-__global__ void __launch_bounds__(DDF_CTA_THREADS)
-k_sptrsm(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64_t nunits, int32_t upc,
-         const int32_t* __restrict__ seq, const int32_t* __restrict__ st, const int32_t* __restrict__ col,
-         const TV* __restrict__ val, const TX* __restrict__ dinv, const TX* __restrict__ B, TX* X, int32_t nrhs,
-         uint32_t* ticket, int32_t* status, int64_t cap_ns) {
+template <typename TV, typename TX, class LY>
+__device__ __forceinline__ void qrow_load(int64_t q, bool act, const int32_t* __restrict__ seq,
+                                          const int32_t* __restrict__ st, const int32_t* __restrict__ col,
+                                          const TV* __restrict__ val, const TX* __restrict__ dinv,
+                                          const TX* __restrict__ B, int32_t nrhs, int lane,
+                                          QRow<TX, LY::VEC>& m) {
+    constexpr int VEC = LY::VEC;
+    m.r = m.kb = m.L = m.pj = 0;
+    m.di = m.pv = (TX)0;
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) m.bv[v] = (TX)0;
+    if (!act) return;
+    m.r = seq[q];
+    m.kb = st[q];
+    m.L = st[q + 1] - m.kb;
+    m.di = dinv[q];
+    const int c = lane % LY::LP;
+    if (c * VEC < nrhs) LY::V::ld_nc(B + (int64_t)m.r * nrhs + c * VEC, m.bv);
+    if (lane < m.L) {
+        m.pv = ddf_cvt<TX>(val[m.kb + lane]);
+        m.pj = col[m.kb + lane];
+    }
+}
+
+// One row: the loads of a sub-block of points (NL per lane, G points per
+// load) are all issued before any is checked, so one L2 round trip covers
+// SUB points of the row; an element still holding the fill pattern is
+// waited on (bounded) before it is used.
+template <typename TV, typename TX, class LY>
+__device__ __forceinline__ void qrow_solve(const QRow<TX, LY::VEC>& m, const int32_t* __restrict__ col,
+                                           const TV* __restrict__ val, TX* X, int32_t nrhs, int lane,
+                                           int32_t* status, uint32_t* abort_flag, int64_t cap_ns) {
+    using V = typename LY::V;
     using RBx = RB<TX>;
-    __shared__ uint32_t chunk;
-    if (threadIdx.x == 0) chunk = atomicAdd(ticket, 1u);
-    __syncthreads();
-    uint32_t* abort_flag = ticket + 1;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t ub = (int64_t)chunk * upc;
-    const int64_t ue = min(ub + (int64_t)upc, nunits);
-    for (int64_t u = ub + w; u < ue; u += DDF_WARPS_PER_CTA) {
-        const dunit U = units[u];
-        const dcod C = cod[U.cod];
-        for (int32_t i0 = U.i0b; i0 < U.i0e; ++i0) {
-            const int32_t q = C.q0 + i0;
-            const int32_t r = (C.flags & DC_F_STRIDED) ? C.f0 + C.rho * i0 : seq[q];
-            int32_t kb, L;
-            if (C.type == DDF_PSC2) {
-                kb = st[q];
-                L = st[q + 1] - kb;
-            } else {
-                kb = C.g0 + C.gamma * i0;
-                L = C.n;
-            }
-            const TX bv = lane < nrhs ? B[(int64_t)r * nrhs + lane] : (TX)0;
-            const TX di = dinv[q];
-            TX acc = 0;
-            for (int32_t p0 = 0; p0 < L; p0 += 32) {
-                const int32_t i1 = p0 + lane;
-                TX pv = 0;
-                int32_t pj = 0;
-                if (i1 < L) {
-                    pv = ddf_cvt<TX>(val[kb + i1]);
-                    pj = point_col(C, col, i0, kb, i1);
+    using U = typename V::U;
+    constexpr int VEC = LY::VEC, G = LY::G, NL = LY::NL, SUB = LY::SUB;
+    const int g = lane / LY::LP, c = lane % LY::LP;
+    const bool on = c * VEC < nrhs;
+    TX acc[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[v] = (TX)0;
+    TX pv = m.pv;
+    int32_t pj = m.pj;
+    for (int32_t p0 = 0; p0 < m.L; p0 += 32) {
+        TX npv = (TX)0;
+        int32_t npj = 0;
+        if (p0 + 32 + lane < m.L) {
+            npv = ddf_cvt<TX>(val[m.kb + p0 + 32 + lane]);
+            npj = col[m.kb + p0 + 32 + lane];
+        }
+        const int32_t cnt = min(32, m.L - p0);
+        for (int32_t s0 = 0; s0 < cnt; s0 += SUB) {
+            U xb[NL][VEC];
+            TX av[NL];
+            int32_t jv[NL];
+#pragma unroll
+            for (int k = 0; k < NL; ++k) {
+                const int t = s0 + k * G + g;
+                av[k] = __shfl_sync(0xffffffffu, pv, t & 31);
+                jv[k] = __shfl_sync(0xffffffffu, pj, t & 31);
+                if (on && t < cnt) {
+                    V::ld_relaxed(X + (int64_t)jv[k] * nrhs + c * VEC, xb[k]);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) xb[k][v] = (U)0;
                 }
-                const int32_t cnt = min(32, L - p0);
-                // the loads of up to SM_E points are issued before any is checked,
-                // so one L2 round trip covers them
-                for (int32_t t0 = 0; t0 < cnt; t0 += SM_E) {
-                    typename RBx::U xv[SM_E];
-                    TX av[SM_E];
-                    int32_t jv[SM_E];
+            }
+            if (on) {
 #pragma unroll
-                    for (int e = 0; e < SM_E; ++e) {
-                        const int32_t t = min(t0 + e, cnt - 1);
-                        av[e] = __shfl_sync(0xffffffffu, pv, t);
-                        jv[e] = __shfl_sync(0xffffffffu, pj, t);
-                        xv[e] = (lane < nrhs && t0 + e < cnt) ? RBx::ld(X + (int64_t)jv[e] * nrhs + lane)
-                                                             : (typename RBx::U)0;
-                    }
-                    if (lane < nrhs) {
+                for (int k = 0; k < NL; ++k) {
+                    if (s0 + k * G + g >= cnt) continue;
+                    TX* xr = X + (int64_t)jv[k] * nrhs + c * VEC;
+                    if constexpr (VEC > 1) {
+                        // the VEC elements were written together: wait for the first one
+                        // still pending, then read all of them again
+                        int pend = -1;
 #pragma unroll
-                        for (int e = 0; e < SM_E; ++e) {
-                            if (t0 + e >= cnt) break;
-                            const TX xj = (xv[e] != RBx::SENT)
-                                              ? RBx::val(xv[e])
-                                              : wait_m<TX>(X + (int64_t)jv[e] * nrhs + lane, status, abort_flag, cap_ns);
-                            acc += av[e] * xj;
+                        for (int v = VEC - 1; v >= 0; --v)
+                            if (xb[k][v] == RBx::SENT) pend = v;
+                        if (pend >= 0) {
+                            (void)wait_m<TX>(xr + pend, status, abort_flag, cap_ns);
+                            V::ld_relaxed(xr, xb[k]);
                         }
                     }
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        const TX xj = (xb[k][v] != RBx::SENT) ? RBx::val(xb[k][v])
+                                                              : wait_m<TX>(xr + v, status, abort_flag, cap_ns);
+                        acc[v] += av[k] * xj;
+                    }
                 }
             }
-            if (lane < nrhs) {
-                const TX xr = (bv - acc) * di;
-                typename RBx::U bits = RBx::bits(xr);
-                if (bits == RBx::SENT) bits = RBx::CANON;
-                RBx::st(X + (int64_t)r * nrhs + lane, bits);
+        }
+        pv = npv;
+        pj = npj;
+    }
+    group_sum<TX, LY::LP, VEC>(acc);
+    if (g == 0 && on) {
+        U bits[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            bits[v] = RBx::bits((m.bv[v] - acc[v]) * m.di);
+            if (bits[v] == RBx::SENT) bits[v] = RBx::CANON;
+        }
+        V::st_relaxed(X + (int64_t)m.r * nrhs + c * VEC, bits);
+    }
+}
+
+// A short row (at most SHORT_ROW points) solved by its own lane group: the
+// LP lanes of group g hold row q's data (QRow, lane c = lane % LP loading
+// point c of each block of NB points), and the group walks the row's points
+// NB at a time, every lane reading its VEC right-hand sides of each point's
+// X row: NB loads per lane in flight together, no cross-lane reduction.  The
+// group's shuffles name only its own lanes, so a group waiting on a
+// dependency does not hold the others back.
+
+template <typename TV, typename TX, class LY>
+__device__ __forceinline__ void grow_load(int64_t q, bool act, const int32_t* __restrict__ seq,
+                                          const int32_t* __restrict__ st, const int32_t* __restrict__ col,
+                                          const TV* __restrict__ val, const TX* __restrict__ dinv,
+                                          const TX* __restrict__ B, int32_t nrhs, int c, QRow<TX, LY::VEC>& m) {
+    constexpr int VEC = LY::VEC, NB = LY::NL;
+    m.r = m.kb = m.L = m.pj = 0;
+    m.di = m.pv = (TX)0;
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) m.bv[v] = (TX)0;
+    if (!act) return;
+    m.r = seq[q];
+    m.kb = st[q];
+    m.L = st[q + 1] - m.kb;
+    m.di = dinv[q];
+    LY::V::ld_nc(B + (int64_t)m.r * nrhs + c * VEC, m.bv);
+    if (c < NB && c < m.L) {
+        m.pv = ddf_cvt<TX>(val[m.kb + c]);
+        m.pj = col[m.kb + c];
+    }
+}
+
+template <typename TV, typename TX, class LY>
+__device__ __forceinline__ void grow_solve(const QRow<TX, LY::VEC>& m, const int32_t* __restrict__ col,
+                                           const TV* __restrict__ val, TX* X, int32_t nrhs, int g, int c,
+                                           int32_t* status, uint32_t* abort_flag, int64_t cap_ns) {
+    using V = typename LY::V;
+    using RBx = RB<TX>;
+    using U = typename V::U;
+    constexpr int VEC = LY::VEC, LP = LY::LP, NB = LY::NL;
+    const unsigned gmask = (LP == 32) ? 0xffffffffu : (((1u << LP) - 1u) << (g * LP));
+    TX acc[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[v] = (TX)0;
+    TX pv = m.pv;
+    int32_t pj = m.pj;
+    for (int32_t p0 = 0; p0 < m.L; p0 += NB) {
+        if (p0 > 0) {
+            pv = (TX)0;
+            pj = 0;
+            if (c < NB && p0 + c < m.L) {
+                pv = ddf_cvt<TX>(val[m.kb + p0 + c]);
+                pj = col[m.kb + p0 + c];
             }
         }
+        const int32_t cnt = min(NB, m.L - p0);
+        U xb[NB][VEC];
+        TX av[NB];
+        int32_t jv[NB];
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+            av[t] = __shfl_sync(gmask, pv, t, LP);
+            jv[t] = __shfl_sync(gmask, pj, t, LP);
+            if (t < cnt) {
+                V::ld_relaxed(X + (int64_t)jv[t] * nrhs + c * VEC, xb[t]);
+            } else {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) xb[t][v] = (U)0;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+            if (t >= cnt) break;
+            TX* xr = X + (int64_t)jv[t] * nrhs + c * VEC;
+            int pend = -1;
+#pragma unroll
+            for (int v = VEC - 1; v >= 0; --v)
+                if (xb[t][v] == RBx::SENT) pend = v;
+            if (pend >= 0) {   // written together: wait for the first pending element, read all again
+                (void)wait_m<TX>(xr + pend, status, abort_flag, cap_ns);
+                V::ld_relaxed(xr, xb[t]);
+            }
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const TX xj = (xb[t][v] != RBx::SENT) ? RBx::val(xb[t][v])
+                                                      : wait_m<TX>(xr + v, status, abort_flag, cap_ns);
+                acc[v] += av[t] * xj;
+            }
+        }
+    }
+    U bits[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+        bits[v] = RBx::bits((m.bv[v] - acc[v]) * m.di);
+        if (bits[v] == RBx::SENT) bits[v] = RBx::CANON;
+    }
+    V::st_relaxed(X + (int64_t)m.r * nrhs + c * VEC, bits);
+}
+
+// Multi-RHS forward substitution over the level-ordered plan.  A persistent
+// grid of warps takes the SpTRSV plan's work units (rows of one codelet, so
+// of one level: they never read one another) from a ticket, each warp on its
+// own, upt consecutive units per ticket (ddf_tune picks upt).  A warp holding
+// unit u waits only on rows of units before u, which running warps hold or
+// have finished, so the lowest unfinished unit can always proceed (no
+// co-residency needed, no cooperative launch).  Inside a unit, G rows at a
+// time: when all of them have at most SHORT_ROW points, one row per lane
+// group; otherwise one row after another on the whole warp, the G groups
+// splitting each row's points.  The next rows' data load while the current
+// ones are solved, and the next ticket is taken before the current units
+// start.  Row x[r] is ready once its elements no longer hold the fill
+// pattern; each lane waits on its own elements.
+template <typename TV, typename TX, class LY>
+__global__ void __launch_bounds__(DDF_CTA_THREADS)
+k_sptrsm(int32_t n, int64_t nunits, int32_t upt, const int32_t* __restrict__ unit_q,
+         const int32_t* __restrict__ seq, const int32_t* __restrict__ st, const int32_t* __restrict__ col,
+         const TV* __restrict__ val,
+         const TX* __restrict__ dinv, const TX* __restrict__ B, TX* X, int32_t nrhs, uint32_t* ticket,
+         int32_t* status, int64_t cap_ns) {
+    constexpr int G = LY::G, LP = LY::LP, VEC = LY::VEC;
+    uint32_t* abort_flag = ticket + 1;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / LP, c = lane % LP;
+    auto take = [&]() -> int64_t {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(ticket, 1u);
+        return (int64_t)__shfl_sync(0xffffffffu, t, 0);
+    };
+    int64_t t = take();
+    while (t * upt < nunits) {
+        const int64_t t_next = take();
+        const int64_t u1 = min(t * upt + upt, nunits);
+        for (int64_t u = t * upt; u < u1; ++u) {   // units in order: each one's rows share a level
+            const int64_t qa = unit_q[u];
+            const int64_t qz = (u + 1 < nunits) ? (int64_t)unit_q[u + 1] : (int64_t)n;
+            if constexpr (LP == 32) {
+                // one element per lane: rows one after another, points split over the warp
+                QRow<TX, VEC> ma, mb;
+                int64_t q = qa;
+                qrow_load<TV, TX, LY>(q, q < qz, seq, st, col, val, dinv, B, nrhs, lane, ma);
+                for (; q < qz; q += 2) {
+                    qrow_load<TV, TX, LY>(q + 1, q + 1 < qz, seq, st, col, val, dinv, B, nrhs, lane, mb);
+                    qrow_solve<TV, TX, LY>(ma, col, val, X, nrhs, lane, status, abort_flag, cap_ns);
+                    if (q + 1 >= qz) break;
+                    qrow_load<TV, TX, LY>(q + 2, q + 2 < qz, seq, st, col, val, dinv, B, nrhs, lane, ma);
+                    qrow_solve<TV, TX, LY>(mb, col, val, X, nrhs, lane, status, abort_flag, cap_ns);
+                }
+            } else {
+                QRow<TX, VEC> cur, nxt;
+                grow_load<TV, TX, LY>(qa + g, qa + g < qz, seq, st, col, val, dinv, B, nrhs, c, cur);
+                for (int64_t s0 = qa; s0 < qz; s0 += G) {
+                    grow_load<TV, TX, LY>(s0 + G + g, s0 + G + g < qz, seq, st, col, val, dinv, B, nrhs, c,
+                                          nxt);
+                    if (!__any_sync(0xffffffffu, cur.L > SHORT_ROW)) {
+                        if (s0 + g < qz)
+                            grow_solve<TV, TX, LY>(cur, col, val, X, nrhs, g, c, status, abort_flag, cap_ns);
+                    } else {
+                        // the G rows in order on the whole warp; row h's data comes from group h
+                        for (int h = 0; h < G; ++h) {
+                            if (s0 + h >= qz) break;
+                            QRow<TX, VEC> m;
+                            const int src = h * LP + c;
+                            m.r = __shfl_sync(0xffffffffu, cur.r, src);
+                            m.kb = __shfl_sync(0xffffffffu, cur.kb, src);
+                            m.L = __shfl_sync(0xffffffffu, cur.L, src);
+                            m.di = __shfl_sync(0xffffffffu, cur.di, src);
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) m.bv[v] = __shfl_sync(0xffffffffu, cur.bv[v], src);
+                            m.pv = (TX)0;
+                            m.pj = 0;
+                            if (lane < m.L) {
+                                m.pv = ddf_cvt<TX>(val[m.kb + lane]);
+                                m.pj = col[m.kb + lane];
+                            }
+                            qrow_solve<TV, TX, LY>(m, col, val, X, nrhs, lane, status, abort_flag, cap_ns);
+                        }
+                    }
+                    cur = nxt;
+                }
+            }
+        }
+        t = t_next;
     }
 }
 
@@ -258,26 +739,69 @@ unsigned grid_units(int64_t nunits, int sm) {
     return (unsigned)std::max<int64_t>(1, std::min(ctas, cap));
 }
 
-template <typename TV, typename TX>
-ddf_status launch_spmm(ddf_plan_s* p, const TV* val, const TX* X, TX* Y, int32_t nrhs, cudaStream_t s) {
-    const int sm = p->sm_count > 0 ? p->sm_count : 152;
+// Lanes per row of X for the 16-byte form (nrhs = VEC * LP, LP a power of two
+// from 2 to 16, blocks 16-byte aligned), else 0 (one element per lane).
+template <typename TX>
+int vector_lp(int32_t nrhs, const void* a, const void* b) {
+    constexpr int VEC = 16 / (int)sizeof(TX);
+    if (nrhs % VEC || ((uintptr_t)a & 15u) || ((uintptr_t)b & 15u)) return 0;
+    const int lp = nrhs / VEC;
+    return (lp == 2 || lp == 4 || lp == 8 || (lp == 16 && VEC == 2)) ? lp : 0;
+}
+
+template <typename TV, typename TX, class LY>
+int launch_spmm_as(ddf_plan_s* p, const TV* val, const TX* X, TX* Y, int32_t nrhs, cudaStream_t s, int sm) {
     int launches = 0;
     for (int t = 0; t < 3; ++t) {
         if (p->nunits[t] <= 0) continue;
-        k_spmm<TV, TX><<<grid_units(p->nunits[t], sm), DDF_CTA_THREADS, 0, s>>>(
+        k_spmm<TV, TX, LY><<<grid_units(p->nunits[t], sm), DDF_CTA_THREADS, 0, s>>>(
             p->cod, p->units[t], p->nunits[t], p->starts, p->col, val, X, Y, nrhs);
         ddf_count_launch();
         ++launches;
     }
     for (int t = 0; t < 2; ++t) {
         if (p->ntiles[t] <= 0) continue;
-        k_spmm_tile<TV, TX><<<grid_units(p->ntiles[t], sm), DDF_CTA_THREADS, 0, s>>>(
+        k_spmm_tile<TV, TX, LY><<<grid_units(p->ntiles[t], sm), DDF_CTA_THREADS, 0, s>>>(
             p->cod, p->tiles[t], p->ntiles[t], p->starts, p->col, val, X, Y, nrhs);
         ddf_count_launch();
         ++launches;
     }
+    return launches;
+}
+
+template <typename TV, typename TX>
+ddf_status launch_spmm(ddf_plan_s* p, const TV* val, const TX* X, TX* Y, int32_t nrhs, cudaStream_t s) {
+    constexpr int VEC = 16 / (int)sizeof(TX);
+    const int sm = p->sm_count > 0 ? p->sm_count : 152;
+    int launches = 0;
+    switch (vector_lp<TX>(nrhs, X, Y)) {
+        case 2: launches = launch_spmm_as<TV, TX, Lay<TX, VEC, 2>>(p, val, X, Y, nrhs, s, sm); break;
+        case 4: launches = launch_spmm_as<TV, TX, Lay<TX, VEC, 4>>(p, val, X, Y, nrhs, s, sm); break;
+        case 8: launches = launch_spmm_as<TV, TX, Lay<TX, VEC, 8>>(p, val, X, Y, nrhs, s, sm); break;
+        case 16:
+            if constexpr (VEC == 2) launches = launch_spmm_as<TV, TX, Lay<TX, VEC, 16>>(p, val, X, Y, nrhs, s, sm);
+            break;
+        default: launches = launch_spmm_as<TV, TX, Lay<TX, 1, 32>>(p, val, X, Y, nrhs, s, sm);
+    }
     p->last_launches = launches;
     DDF_CUDA_TRY(cudaGetLastError());
+    return DDF_OK;
+}
+
+template <typename TV, typename TX, class LY>
+ddf_status launch_sptrsm_as(ddf_plan_s* p, const TV* val, const TX* dinv, const TX* B, TX* X, int32_t nrhs,
+                            cudaStream_t s, int sm) {
+    const auto kern = k_sptrsm<TV, TX, LY>;
+    int per_sm = 0;
+    DDF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, DDF_CTA_THREADS, 0));
+    const int32_t upt = p->mrhs_units_per_ticket > 0 ? p->mrhs_units_per_ticket : 1;
+    const int64_t tickets = (p->nunits[0] + upt - 1) / upt;
+    const int64_t want = (tickets + DDF_WARPS_PER_CTA - 1) / DDF_WARPS_PER_CTA;
+    const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm * std::max(per_sm, 1)));
+    kern<<<(unsigned)ctas, DDF_CTA_THREADS, 0, s>>>(p->n, p->nunits[0], upt, p->unit_q, p->seq, p->starts, p->col,
+                                                   val, dinv, B, X, nrhs, p->ticket, p->status,
+                                                   p->opts.spin_cap_ns);
+    ddf_count_launch();
     return DDF_OK;
 }
 
@@ -285,23 +809,27 @@ template <typename TV, typename TX>
 ddf_status launch_sptrsm(ddf_plan_s* p, const TV* val, const TX* dinv, const TX* B, TX* X, int32_t nrhs,
                          cudaStream_t s) {
     using RBx = RB<TX>;
+    constexpr int VEC = 16 / (int)sizeof(TX);
     const int sm = p->sm_count > 0 ? p->sm_count : 152;
     const int64_t ne = (int64_t)p->n * nrhs;
     k_fill_m<typename RBx::U><<<ddf_grid(ne > 0 ? ne : 1, 256, (unsigned)sm * 8), 256, 0, s>>>(
         (typename RBx::U*)X, ne, RBx::SENT, p->ticket);
     ddf_count_launch();
-    int launches = 1;
-    const int64_t nu = p->nunits[0];
-    if (nu > 0) {
-        const int32_t upc = p->units_per_cta > 0 ? p->units_per_cta : DDF_WARPS_PER_CTA;
-        const int64_t ctas = (nu + upc - 1) / upc;
-        k_sptrsm<TV, TX><<<(unsigned)ctas, DDF_CTA_THREADS, 0, s>>>(p->cod, p->units[0], nu, upc, p->seq,
-                                                                    p->starts, p->col, val, dinv, B, X, nrhs,
-                                                                    p->ticket, p->status, p->opts.spin_cap_ns);
-        ddf_count_launch();
-        ++launches;
+    ddf_status st = DDF_OK;
+    if (p->nunits[0] > 0) {
+        switch (vector_lp<TX>(nrhs, B, X)) {
+            case 2: st = launch_sptrsm_as<TV, TX, Lay<TX, VEC, 2>>(p, val, dinv, B, X, nrhs, s, sm); break;
+            case 4: st = launch_sptrsm_as<TV, TX, Lay<TX, VEC, 4>>(p, val, dinv, B, X, nrhs, s, sm); break;
+            case 8: st = launch_sptrsm_as<TV, TX, Lay<TX, VEC, 8>>(p, val, dinv, B, X, nrhs, s, sm); break;
+            case 16:
+                if constexpr (VEC == 2)
+                    st = launch_sptrsm_as<TV, TX, Lay<TX, VEC, 16>>(p, val, dinv, B, X, nrhs, s, sm);
+                break;
+            default: st = launch_sptrsm_as<TV, TX, Lay<TX, 1, 32>>(p, val, dinv, B, X, nrhs, s, sm);
+        }
     }
-    p->last_launches = launches;
+    if (st) return st;
+    p->last_launches = 2;
     DDF_CUDA_TRY(cudaGetLastError());
     return DDF_OK;
 }
@@ -443,19 +971,19 @@ ddf_status ddf_tune(ddf_plan_t p, const void* in, void* out, int32_t nrhs, ddf_d
     cudaEvent_t e0, e1;
     DDF_CUDA_TRY(cudaEventCreate(&e0));
     DDF_CUDA_TRY(cudaEventCreate(&e1));
-    // SpMV: tile size of the work units; SpTRSV: work units per CTA ticket
+    // SpMV: tile size of the work units; SpTRSV: work units per warp ticket
     const int32_t cand_spmv[] = {64, 128, 256, 512, 1024, 2048};
-    const int32_t cand_trsv[] = {8, 16, 32, 64};
+    const int32_t cand_trsv[] = {1, 2, 4, 8};
     const bool spmv = p->kind == DDF_SPMV;
     const int nc = spmv ? 6 : 4;
     float best = 3.0e38f;
-    int32_t pick = spmv ? p->opts.unit_nnz : p->units_per_cta;
+    int32_t pick = spmv ? p->opts.unit_nnz : p->mrhs_units_per_ticket;
     for (int c = 0; c < nc && !st; ++c) {
         if (spmv) {
             p->opts.unit_nnz = cand_spmv[c];
             st = ddf_build_units(p, s);
         } else {
-            p->units_per_cta = cand_trsv[c];
+            p->mrhs_units_per_ticket = cand_trsv[c];
         }
         if (st) break;
         float ms = 0.0f;
@@ -477,7 +1005,7 @@ ddf_status ddf_tune(ddf_plan_t p, const void* in, void* out, int32_t nrhs, ddf_d
         p->opts.unit_nnz = pick;
         if (!st) st = ddf_build_units(p, s);
     } else {
-        p->units_per_cta = pick;
+        p->mrhs_units_per_ticket = pick;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

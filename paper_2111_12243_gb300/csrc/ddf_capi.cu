@@ -126,7 +126,7 @@ ddf_status ddf_new_plan(ddf_kind kind, const ddf_opts* o, cudaStream_t s, int32_
     p->n = n;
     p->n_cols = n_cols;
     p->nnz = nnz;
-    p->units_per_cta = DDF_WARPS_PER_CTA;
+    p->mrhs_units_per_ticket = 1;
     if (cudaGetDevice(&p->device) != cudaSuccess) {
         (void)cudaGetLastError();
         delete p;

@@ -115,7 +115,7 @@ struct ddf_plan_s {
     int32_t* status;              // device status word (ddf_status)
     uint32_t* ticket;             // SpTRSV: work ticket
     int32_t last_launches;
-    int32_t units_per_cta;
+    int32_t mrhs_units_per_ticket;   // ddf_sptrsm: work units per warp ticket (ddf_tune picks it)
     int32_t sm_count;
     // mixed precision (store_dtype != DDF_F64): low-precision copies and the
     // refinement scratch of a SpTRSV plan

@@ -56,56 +56,185 @@ __global__ void k_rhs(const double* __restrict__ b, float* __restrict__ blp, int
 
 // r = b - L x in FP64 over the level-ordered copy: position q holds row
 // seq[q], its off-diagonal entries starts[q] .. starts[q+1] and L_qq = diag[q].
-// Also ||r||^2 and r rounded to FP32.  A thread sums a row of up to
-// RES_LONG off-diagonal entries by itself (one FP64 multiply-add per entry,
-// no reduction); longer rows (the power-law matrix has rows of thousands of
-// entries) are collected by a ballot and summed by the whole warp, lanes
-// striding over the entries.  The sum of squares goes to nrm[1]; thread 0
-// also copies the plan's status word into nrm[2], so that one copy returns
-// the norms and the solve's status.
-constexpr int32_t RES_LONG = 64;
+// Also ||r||^2 (into nrm[1]) and r rounded to FP32.  The positions are cut
+// into groups of 32; a group of T points runs on NT threads (a warp, or the
+// whole CTA when T > RES_WARP_MAX), thread t adding the products of the
+// points [t K, (t + 1) K), K = ceil(T / NT), row by row with fused
+// multiply-adds in point order, four points' loads in flight at a time.  A
+// scan over the threads carries the partial sums of rows that cross stretch
+// boundaries to the thread where each row ends, so any mix of row lengths
+// (the power-law matrix has rows of thousands of entries next to rows of
+// one) spreads evenly over the threads, and every sum has a fixed order.
+// Thread 0 also copies the plan's status word into nrm[2], so that one copy
+// returns the norms and the solve's status.
+constexpr int RES_ROWS = 32;
+constexpr int RES_WARP_MAX = 2048;
+constexpr int RES_THREADS = 256;
 
-__global__ void k_residual(int32_t n, const int32_t* __restrict__ seq, const int32_t* __restrict__ st,
-                           const int32_t* __restrict__ col, const double* __restrict__ val,
-                           const double* __restrict__ diag, const double* __restrict__ b,
-                           const double* __restrict__ x, double* __restrict__ r, float* __restrict__ rlp,
-                           double* __restrict__ nrm, const int32_t* __restrict__ status) {
-    const int lane = threadIdx.x & 31;
+struct ResArgs {
+    const int32_t* seq;
+    const int32_t* st;
+    const int32_t* col;
+    const double* val;
+    const double* diag;
+    const double* b;
+    const double* x;
+    double* r;
+    float* rlp;
+};
+
+__device__ __forceinline__ void res_finish(const ResArgs& A, int32_t q, double sum, double& s2) {
+    const int32_t row = A.seq[q];
+    const double rv = A.b[row] - (A.diag[q] * A.x[row] + sum);
+    A.r[row] = rv;
+    A.rlp[row] = (float)rv;
+    s2 += rv * rv;
+}
+
+// One group of R positions starting at qa, its points (relative to st[qa])
+// bounded by srow[0 .. R]; NT threads, t = this thread's index among them.
+// wb / wa: per-warp scan totals (NT > 32 only).
+template <int NT>
+__device__ __forceinline__ void res_group(const ResArgs& A, int32_t qa, int32_t R, const int32_t* srow, int t,
+                                          double* wb, int32_t* wa, double& s2) {
+    const int lane = t & 31;
+    const int32_t ka = A.st[qa];
+    const int32_t T = srow[R];
+    if (t < R && srow[t + 1] == srow[t]) res_finish(A, qa + t, 0.0, s2);   // rows without off-diagonals
+    const int32_t K = (T + NT - 1) / NT;
+    const int32_t e0 = min(t * K, T), e1 = min(e0 + K, T);
+    double hp = 0.0, tp = 0.0;
+    int32_t hr = 0, tr = 0;
+    bool cont = false, single = true;
+    if (e0 < e1) {
+        int32_t lo = 0, hi = R - 1;   // the row holding point e0: the last row starting at or before it
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (srow[mid] <= e0) lo = mid;
+            else hi = mid - 1;
+        }
+        int32_t rr = lo;
+        hr = rr;
+        cont = srow[rr] < e0;
+        int32_t e = e0;
+        while (true) {
+            const int32_t end = min(srow[rr + 1], e1);
+            double acc = 0.0;
+            int32_t k = e;
+            for (; k + 4 <= end; k += 4) {
+                const int64_t z = (int64_t)ka + k;
+                const double v0 = A.val[z], v1 = A.val[z + 1], v2 = A.val[z + 2], v3 = A.val[z + 3];
+                const double x0 = A.x[A.col[z]], x1 = A.x[A.col[z + 1]], x2 = A.x[A.col[z + 2]],
+                             x3 = A.x[A.col[z + 3]];
+                acc = fma(v0, x0, acc);
+                acc = fma(v1, x1, acc);
+                acc = fma(v2, x2, acc);
+                acc = fma(v3, x3, acc);
+            }
+            for (; k < end; ++k) acc = fma(A.val[(int64_t)ka + k], A.x[A.col[(int64_t)ka + k]], acc);
+            if (rr == hr) hp = acc;
+            if (end == e1) {
+                tr = rr;
+                tp = acc;
+                break;
+            }
+            if (rr != hr) res_finish(A, qa + rr, acc, s2);   // a row inside the stretch
+            single = false;
+            e = end;
+            do {
+                ++rr;
+            } while (srow[rr + 1] == srow[rr]);   // skip rows without points (a later row holds point e)
+        }
+    }
+    // carry_out(t) = tp(t) + [single(t) and cont(t)] carry_out(t - 1): a scan over the threads
+    double cb = tp;
+    bool ca = single && cont && e0 < e1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double pb = __shfl_up_sync(0xffffffffu, cb, o);
+        const bool pa = __shfl_up_sync(0xffffffffu, ca, o);
+        if (lane >= o) {
+            if (ca) cb += pb;
+            ca = ca && pa;
+        }
+    }
+    double cin;
+    if constexpr (NT == 32) {
+        const double prev = __shfl_up_sync(0xffffffffu, cb, 1);
+        cin = (lane > 0 && cont) ? prev : 0.0;
+    } else {
+        const int w = t >> 5;
+        if (lane == 31) {
+            wb[w] = cb;
+            wa[w] = ca;
+        }
+        __syncthreads();
+        double cw = 0.0;   // carry into this warp, warps combined in index order
+        for (int i = 0; i < w; ++i) cw = wb[i] + (wa[i] ? cw : 0.0);
+        const double out = cb + (ca ? cw : 0.0);
+        const double prev = __shfl_up_sync(0xffffffffu, out, 1);
+        cin = cont ? (lane > 0 ? prev : cw) : 0.0;
+        __syncthreads();
+    }
+    if (e0 < e1) {
+        if (!single) {
+            res_finish(A, qa + hr, hp + cin, s2);   // the head row ended in the stretch
+            if (srow[tr + 1] == e1) res_finish(A, qa + tr, tp, s2);
+        } else if (srow[hr + 1] == e1) {
+            res_finish(A, qa + hr, hp + cin, s2);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(RES_THREADS)
+k_residual(int32_t n, ResArgs A, double* __restrict__ nrm, const int32_t* __restrict__ status) {
+    constexpr int NWARP = RES_THREADS / 32;
+    __shared__ int32_t srow_w[NWARP][RES_ROWS + 1];
+    __shared__ int32_t srow_c[RES_ROWS + 1];
+    __shared__ int32_t heavy[RES_THREADS];
+    __shared__ int32_t nheavy;
+    __shared__ double wb[NWARP];
+    __shared__ int32_t wa[NWARP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (blockIdx.x == 0 && threadIdx.x == 0) reinterpret_cast<int32_t*>(nrm + 2)[0] = *status;
     double s2 = 0.0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // the loop runs the same number of times on every lane of a warp
-    const int64_t q_end = ((int64_t)n + 31) / 32 * 32;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < q_end; q += stride) {
-        const bool in = q < n;
-        int32_t a = 0, e = 0, row = 0;
-        if (in) {
-            row = seq[q];
-            a = st[q];
-            e = st[q + 1];
+    const int64_t ngroups = ((int64_t)n + RES_ROWS - 1) / RES_ROWS;
+    auto group_points = [&](int64_t g) {
+        const int32_t qa = (int32_t)(g * RES_ROWS);
+        const int32_t R = min(RES_ROWS, n - qa);
+        return A.st[qa + R] - A.st[qa];
+    };
+    // groups of more than RES_WARP_MAX points: one CTA each.  This CTA looks
+    // at groups blockIdx.x + i gridDim.x, 256 values of i at a time, and runs
+    // the heavy ones among them (the long rows of a power-law matrix sit at
+    // its deep levels, so heavy groups cluster in level order: the stride
+    // spreads them over the CTAs).
+    for (int64_t i0 = 0; (int64_t)blockIdx.x + i0 * gridDim.x < ngroups; i0 += RES_THREADS) {
+        if (threadIdx.x == 0) nheavy = 0;
+        __syncthreads();
+        const int64_t g = (int64_t)blockIdx.x + (i0 + threadIdx.x) * gridDim.x;
+        if (g < ngroups && group_points(g) > RES_WARP_MAX) heavy[atomicAdd(&nheavy, 1)] = (int32_t)g;
+        __syncthreads();
+        const int32_t nh = nheavy;
+        for (int32_t h = 0; h < nh; ++h) {
+            const int32_t qa = heavy[h] * RES_ROWS;
+            const int32_t R = min(RES_ROWS, n - qa);
+            if ((int)threadIdx.x <= R) srow_c[threadIdx.x] = A.st[qa + threadIdx.x] - A.st[qa];
+            __syncthreads();
+            res_group<RES_THREADS>(A, qa, R, srow_c, threadIdx.x, wb, wa, s2);
+            __syncthreads();
         }
-        const bool lng = in && e - a > RES_LONG;
-        double acc = 0.0;
-        if (in && !lng) {
-            acc = diag[q] * x[row];
-            for (int32_t k = a; k < e; ++k) acc += val[k] * x[col[k]];
-        }
-        // long rows: the warp sums each in turn
-        for (unsigned m = __ballot_sync(0xffffffffu, lng); m; m &= m - 1) {
-            const int src = __ffs(m) - 1;
-            const int32_t la = __shfl_sync(0xffffffffu, a, src), le = __shfl_sync(0xffffffffu, e, src);
-            double part = 0.0;
-            for (int32_t k = la + lane; k < le; k += 32) part += val[k] * x[col[k]];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-            if (lane == src) acc = diag[q] * x[row] + part;
-        }
-        if (in) {
-            const double rv = b[row] - acc;
-            r[row] = rv;
-            rlp[row] = (float)rv;
-            s2 += rv * rv;
-        }
+    }
+    // the other groups: one warp each
+    int32_t* srow = srow_w[w];
+    const int64_t nw = ((int64_t)gridDim.x * RES_THREADS) >> 5;
+    for (int64_t g = ((int64_t)blockIdx.x * RES_THREADS + threadIdx.x) >> 5; g < ngroups; g += nw) {
+        const int32_t qa = (int32_t)(g * RES_ROWS);
+        const int32_t R = min(RES_ROWS, n - qa);
+        for (int32_t i = lane; i <= R; i += 32) srow[i] = A.st[qa + i] - A.st[qa];
+        __syncwarp();
+        if (srow[R] <= RES_WARP_MAX) res_group<32>(A, qa, R, srow, lane, nullptr, nullptr, s2);
+        __syncwarp();
     }
     block_add(s2, nrm + 1);
 }
@@ -177,8 +306,9 @@ ddf_status ddf_refine(ddf_plan_s* p, const double* b, double* x, double tol, int
     int32_t it = 0;
     for (;; ++it) {
         DDF_CUDA_TRY(cudaMemsetAsync(p->nrm + 1, 0, sizeof(double), s));
-        k_residual<<<gs(n, sm), 256, 0, s>>>((int32_t)n, p->seq, p->starts, p->col, p->val, p->diag, b, x, p->r64,
-                                            p->rlp, p->nrm, p->status);
+        const ResArgs ra{p->seq, p->starts, p->col, p->val, p->diag, b, x, p->r64, p->rlp};
+        k_residual<<<ddf_grid(((n + 31) / 32) * 32, RES_THREADS, (unsigned)sm * 8), RES_THREADS, 0, s>>>(
+            (int32_t)n, ra, p->nrm, p->status);
         ddf_count_launch();
         ++launches;
         // the norms and the solve's status word in one copy, one wait per step

@@ -21,7 +21,7 @@ constexpr int32_t VERSION = 5;
 
 struct Header {
     char magic[8];
-    int32_t version, kind, n, n_cols, depth, has_values, vdtype, units_per_cta;
+    int32_t version, kind, n, n_cols, depth, has_values, vdtype, mrhs_units_per_ticket;
     int32_t nlevels, nblocks;
     int64_t nnz, npts, ncod, ncod_type[3], nunits[3], nchunks;
     int64_t ntiles[2];
@@ -101,7 +101,7 @@ Header header_of(ddf_plan_s* p) {
     h.depth = p->depth;
     h.has_values = p->has_values;
     h.vdtype = p->vdtype;
-    h.units_per_cta = p->units_per_cta;
+    h.mrhs_units_per_ticket = p->mrhs_units_per_ticket;
     h.nlevels = p->nlevels;
     h.nblocks = p->nblocks;
     h.nchunks = p->nchunks;
@@ -188,7 +188,7 @@ ddf_status ddf_plan_load(const void* buf, size_t len, ddf_stream_t stream, ddf_p
     p->ncod = h.ncod;
     p->has_values = h.has_values;
     p->vdtype = h.vdtype;
-    p->units_per_cta = h.units_per_cta;
+    p->mrhs_units_per_ticket = h.mrhs_units_per_ticket;
     p->nlevels = h.nlevels;
     p->nblocks = h.nblocks;
     p->nchunks = h.nchunks;

@@ -334,16 +334,31 @@ k_spmv_psc2(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64
             cont = srow[r] < e0;
             TA acc = 0;
             int32_t next = srow[r + 1];
-            for (int32_t e = e0; e < e1; ++e) {
-                while (next <= e) {   // row r ended before point e
-                    if (single) hp = acc;
-                    else if (next > srow[r]) y[fb + C.rho * r] = store_cvt<TY, TA>(acc);   // inside the stretch
-                    single = false;
-                    acc = 0;
-                    ++r;
-                    next = srow[r + 1];
+            for (int32_t eb = e0; eb < e1; eb += 4) {
+                // four points' loads in flight together, then their multiply-adds in point order
+                TA pa[4], px[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    pa[i] = px[i] = (TA)0;
+                    if (eb + i < e1) {
+                        pa[i] = ddf_cvt<TA>(__ldcs(val + ka + eb + i));
+                        px[i] = ddf_cvt<TA>(__ldg(x + __ldcs(col + ka + eb + i)));
+                    }
                 }
-                acc += ddf_cvt<TA>(__ldcs(val + ka + e)) * ddf_cvt<TA>(__ldg(x + __ldcs(col + ka + e)));
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int32_t e = eb + i;
+                    if (e >= e1) break;
+                    while (next <= e) {   // row r ended before point e
+                        if (single) hp = acc;
+                        else if (next > srow[r]) y[fb + C.rho * r] = store_cvt<TY, TA>(acc);   // inside the stretch
+                        single = false;
+                        acc = 0;
+                        ++r;
+                        next = srow[r + 1];
+                    }
+                    acc += pa[i] * px[i];
+                }
             }
             tr = r;
             tp = acc;

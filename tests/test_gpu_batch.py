@@ -74,7 +74,9 @@ def test_batch_plans_equal_block_diagonal_inspection(small_batch, on_device):
         assert oracle.check_plan(bd, okind, got["seq"], got["part_ptr"], got["gs"], got["records"]) == (0, -1)
 
 
-@pytest.mark.parametrize("nrhs", [1, 5, 32])
+# nrhs 4, 8, 16, 32 run the vector executors (2 right-hand sides per lane,
+# 2 .. 16 lanes per row of X), 1 and 5 the scalar ones
+@pytest.mark.parametrize("nrhs", [1, 4, 5, 8, 16, 32])
 def test_spmm_and_sptrsm_f64(small_batch, nrhs):
     bd = block_diag(small_batch)
     lo = block_diag([synth.lower_triangle(m) for m in small_batch])
@@ -97,17 +99,30 @@ def test_spmm_and_sptrsm_f64(small_batch, nrhs):
         assert np.linalg.norm(Xh[:, k] - rx) <= TOL * np.linalg.norm(rx)
 
 
-def test_spmm_and_sptrsm_f32(small_batch):
-    nrhs = 32
+def f32_block(a, shift):
+    """a on the device, starting `shift` floats past a 16-byte boundary."""
+    flat = torch.zeros(a.size + 4, dtype=torch.float32, device="cuda")
+    v = flat[shift:shift + a.size].view(a.shape)
+    v.copy_(torch.from_numpy(np.ascontiguousarray(a)))
+    return v
+
+
+# nrhs 8, 16, 32 on aligned blocks run the vector executors (4 right-hand
+# sides per lane); shifted blocks and nrhs 3 the scalar ones
+@pytest.mark.parametrize("nrhs,shift", [(32, 0), (16, 0), (8, 0), (32, 1), (3, 0)])
+def test_spmm_and_sptrsm_f32(small_batch, nrhs, shift):
     bd = block_diag(small_batch)
     lo = block_diag([synth.lower_triangle(m) for m in small_batch])
     rng = np.random.default_rng(7)
     X = rng.uniform(-1, 1, (bd.n_cols, nrhs)).astype(np.float32)
     B = rng.uniform(-1, 1, (lo.n_rows, nrhs)).astype(np.float32)
     p = batch_plan(small_batch, ddf.DDF_SPMV, store_dtype=ddf.DDF_F32)
-    Y = torch.empty((bd.n_rows, nrhs), dtype=torch.float32, device="cuda")
-    ddf.ddf_spmm(p, dev(X), Y, nrhs)
+    Y = f32_block(np.zeros((bd.n_rows, nrhs), np.float32), shift)
+    ddf.ddf_spmm(p, f32_block(X, shift), Y, nrhs)
     Yh = Y.double().cpu().numpy()
+    y2 = Y.clone()
+    ddf.ddf_spmm(p, f32_block(X, shift), Y, nrhs)
+    assert torch.equal(Y, y2)                           # fixed summation order
     absa = synth.CSR(bd.n_rows, bd.n_cols, bd.rowptr, bd.colidx, np.abs(bd.values))
     k_row = np.maximum(np.diff(bd.rowptr), 1)
     for k in range(0, nrhs, 7):
@@ -116,10 +131,13 @@ def test_spmm_and_sptrsm_f32(small_batch):
         bound = 2 * k_row * U32 * oracle.spmv(absa, np.abs(xk)) + 1e-30
         assert np.all(np.abs(Yh[:, k] - ref) <= bound)
     q = batch_plan([synth.lower_triangle(m) for m in small_batch], ddf.DDF_SPTRSV, store_dtype=ddf.DDF_F32)
-    Xs = torch.zeros((lo.n_rows, nrhs), dtype=torch.float32, device="cuda")
-    ddf.ddf_sptrsm(q, dev(B), Xs, nrhs)
+    Xs = f32_block(np.zeros((lo.n_rows, nrhs), np.float32), shift)
+    ddf.ddf_sptrsm(q, f32_block(B, shift), Xs, nrhs)
     assert ddf.ddf_get_status(q) == 0
     Xh = Xs.double().cpu().numpy()
+    x2 = Xs.clone()
+    ddf.ddf_sptrsm(q, f32_block(B, shift), Xs, nrhs)
+    assert torch.equal(Xs, x2)
     for k in range(0, nrhs, 5):
         bk = B[:, k].astype(np.float64)
         r = bk - oracle.spmv(lo, Xh[:, k])
@@ -139,7 +157,7 @@ def test_tune_and_graph_capture(small_batch):
     Y = torch.empty((bd.n_rows, nrhs), dtype=torch.float32, device="cuda")
     Xs = torch.empty((lo.n_rows, nrhs), dtype=torch.float32, device="cuda")
     assert ddf.ddf_tune(p, X, Y, nrhs) in (64, 128, 256, 512, 1024, 2048)
-    assert ddf.ddf_tune(q, B, Xs, nrhs) in (8, 16, 32, 64)
+    assert ddf.ddf_tune(q, B, Xs, nrhs) in (1, 2, 4, 8)
     ddf.ddf_spmm(p, X, Y, nrhs)
     ddf.ddf_sptrsm(q, B, Xs, nrhs)
     torch.cuda.synchronize()

@@ -156,10 +156,10 @@ def test_low_precision_tiles(dtype, tol, name):
     assert relerr(yl.double().cpu().numpy(), ref) <= tol
 
 
+@pytest.mark.parametrize("nrhs", [5, 8])
 @pytest.mark.parametrize("name", ["st27_10", "long_rows", "elast_6", "long_psc2"])
-def test_multi_rhs_on_tiled_plan(name):
+def test_multi_rhs_on_tiled_plan(name, nrhs):
     a = CASES[name]()
-    nrhs = 5
     X = np.stack([synth.uniform_vector(a.n_cols, 40 + k) for k in range(nrhs)], axis=1)
     p = ddf.ddf_inspect(dev(a.rowptr), dev(a.colidx), dev(a.values), a.n_cols, ddf.DDF_SPMV)
     Y = torch.empty((a.n_rows, nrhs), dtype=torch.float64, device="cuda")
