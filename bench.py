@@ -591,11 +591,13 @@ def critical_path(t_hop, breakdown, exec_only, hbm, n_chain=8192):
 
 def run_batch(args, ddf, torch, dev, stream, flush, nrhs=32, reps=5):
     """The batching form: 256 uneven matrices (FP32 values), 32 right-hand
-    sides each.  Batched: one block-diagonal plan per kind, tiles picked by
-    ddf_tune, SpMM + SpTRSM recorded in one CUDA graph and replayed.  Compared
-    with per-matrix launches of the same multi-RHS executors and with the
-    plain path (the FP64 single-vector executors, one call per matrix and
-    right-hand side)."""
+    sides each.  Batched: one block-diagonal plan per kind, work shapes picked
+    by ddf_tune, the SpMV and the SpTRSV of the whole batch in one launch
+    (ddf_batch_run, after the solve's fill) recorded in a CUDA graph and
+    replayed.  Compared with the same two executors as separate calls (also
+    in a graph), with per-matrix launches of them, and with the plain path
+    (the FP64 single-vector executors, one call per matrix and right-hand
+    side)."""
     mats, rhs = synth.batch(args.batch_count, nrhs=nrhs)
     lows = [synth.lower_triangle(m) for m in mats]
     td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
@@ -612,16 +614,22 @@ def run_batch(args, ddf, torch, dev, stream, flush, nrhs=32, reps=5):
     tile_trsv = ddf.ddf_tune(pL, X, Xs, nrhs)
     side = torch.cuda.Stream(device=dev)
     side.wait_stream(stream)
-    g = torch.cuda.CUDAGraph()
+    g = torch.cuda.CUDAGraph()           # one launch for both executors
+    g2 = torch.cuda.CUDAGraph()          # the two executors as separate calls
     with torch.cuda.stream(side):
         with torch.cuda.graph(g, stream=side):
+            ddf.ddf_batch_run(pA, X, Y, pL, X, Xs, nrhs, stream=side)
+        launches_one = ddf.ddf_last_launches(pL) + ddf.ddf_last_launches(pA)
+        with torch.cuda.graph(g2, stream=side):
             ddf.ddf_spmm(pA, X, Y, nrhs, stream=side)
             ddf.ddf_sptrsm(pL, X, Xs, nrhs, stream=side)
+        launches_two = ddf.ddf_last_launches(pL) + ddf.ddf_last_launches(pA)
     stream.wait_stream(side)
     timed = make_timer(torch, stream, flush)
 
     t_graph = timed(g.replay, reps)
     st_graph = ddf.ddf_get_status(pL)
+    t_graph2 = timed(g2.replay, reps)
     t_spmm = timed(lambda: ddf.ddf_spmm(pA, X, Y, nrhs), reps)
     t_trsm = timed(lambda: ddf.ddf_sptrsm(pL, X, Xs, nrhs), reps)
     sa, sl = ddf.ddf_plan_stats(pA), ddf.ddf_plan_stats(pL)
@@ -667,8 +675,10 @@ def run_batch(args, ddf, torch, dev, stream, flush, nrhs=32, reps=5):
             "sptrsm_levels": sl["levels"],
             "sptrsm_us_per_level": round(t_trsm * 1e3 / max(sl["levels"], 1), 3),
             "dtype": "f32 values and vectors, f32 sums", "tile_spmm_unit_nnz": tile_spmv,
-            "tile_sptrsm_units_per_cta": tile_trsv, "graph_ms": round(t_graph, 4), "graph_status": st_graph,
+            "tile_sptrsm_units_per_ticket": tile_trsv, "graph_ms": round(t_graph, 4), "graph_status": st_graph,
             "graph_gbs": round((bytes_spmm + bytes_trsm) / (t_graph * 1e-3) / 1e9, 1),
+            "graph_launches": launches_one, "graph_two_calls_ms": round(t_graph2, 4),
+            "graph_two_calls_launches": launches_two,
             "spmm_ms": round(t_spmm, 4), "spmm_gbs": round(bytes_spmm / (t_spmm * 1e-3) / 1e9, 1),
             "sptrsm_ms": round(t_trsm, 4), "sptrsm_gbs": round(bytes_trsm / (t_trsm * 1e-3) / 1e9, 1),
             "per_matrix_multi_rhs_ms": round(t_per, 3), "speedup_vs_per_matrix": round(t_per / t_graph, 2),

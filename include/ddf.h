@@ -263,6 +263,24 @@ DDF_API ddf_status ddf_sptrsm(ddf_plan_t p, const void* B, void* X, int32_t nrhs
                               ddf_stream_t s);
 
 /*
+ * A batch's SpMV and SpTRSV in one persistent launch (after the fill of Xs
+ * that marks its rows unsolved): Y = A X on the SpMV plan pa and L Xs = B on
+ * the SpTRSV plan pl, both typically from ddf_inspect_batch, with nrhs
+ * (1..32) right-hand sides; layouts and dtypes as in ddf_spmm / ddf_sptrsm
+ * (DDF_F32 needs both plans stored in FP32).  The warps of the launch take
+ * tickets: first the solve's work units, in level order, then the SpMV's
+ * work items, so the products run on the warps the solve's narrow deep
+ * levels leave idle.  Results equal those of ddf_spmm and ddf_sptrsm on the
+ * same operands.  Xs must not overlap X, Y or B, and Y must not overlap X or
+ * B (DDF_ERR_ARG).  DDF_ERR_WRONG_KIND unless pa is DDF_SPMV and pl
+ * DDF_SPTRSV.  Solve errors (DDF_ERR_TIMEOUT) are latched in pl's status
+ * word (ddf_get_status).  Plain launches only, so the call can be recorded
+ * in a CUDA graph.
+ */
+DDF_API ddf_status ddf_batch_run(ddf_plan_t pa, const void* X, void* Y, ddf_plan_t pl, const void* B, void* Xs,
+                                 int32_t nrhs, ddf_dtype dtype, ddf_stream_t s);
+
+/*
  * Autotuner for the multi-RHS executors.  Kind DDF_SPMV: rebuilds the plan's
  * work units for each candidate tile size (target nonzeros per unit: 64 ..
  * 2048) and times ddf_spmm; kind DDF_SPTRSV: times ddf_sptrsm for each

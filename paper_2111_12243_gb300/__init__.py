@@ -35,8 +35,8 @@ EXPORTS = ("ddf_opts_default", "ddf_inspect", "ddf_update_values", "ddf_spmv", "
            "ddf_get_status", "ddf_plan_stats", "ddf_plan_export", "ddf_plan_destroy",
            "ddf_status_string", "ddf_last_launches", "ddf_kernel_launches",
            "ddf_debug_set_dependency", "ddf_sptrsv_csr_noalloc", "ddf_spmv_lowp", "ddf_sptrsv_refine",
-           "ddf_inspect_batch", "ddf_spmm", "ddf_sptrsm", "ddf_tune", "ddf_plan_save", "ddf_plan_load",
-           "ddf_plan_validate", "ddf_debug_fail_alloc")
+           "ddf_inspect_batch", "ddf_spmm", "ddf_sptrsm", "ddf_batch_run", "ddf_tune", "ddf_plan_save",
+           "ddf_plan_load", "ddf_plan_validate", "ddf_debug_fail_alloc")
 #: rows accepted by ddf_sptrsv_csr_noalloc (the size of its static scratch)
 DDF_NOALLOC_MAX_ROWS = 1 << 20
 DDF_COARSEN_MAX_ROWS = 16384
@@ -119,6 +119,8 @@ def lib():
         L.ddf_spmm.restype = ctypes.c_int
         L.ddf_sptrsm.argtypes = [P, P, P, I32, ctypes.c_int, P]
         L.ddf_sptrsm.restype = ctypes.c_int
+        L.ddf_batch_run.argtypes = [P, P, P, P, P, P, I32, ctypes.c_int, P]
+        L.ddf_batch_run.restype = ctypes.c_int
         L.ddf_tune.argtypes = [P, P, P, I32, ctypes.c_int, P, ctypes.POINTER(I32)]
         L.ddf_tune.restype = ctypes.c_int
         L.ddf_plan_save.argtypes = [P, P, ctypes.POINTER(ctypes.c_size_t)]
@@ -323,6 +325,19 @@ def ddf_sptrsm(plan: Plan, B, X, nrhs: int, stream=None):
     if db != dx:
         raise ValueError("B and X must have the same dtype")
     _check(lib().ddf_sptrsm(plan.handle, pb, px, int(nrhs), db, _stream(stream)), "ddf_sptrsm")
+
+
+def ddf_batch_run(pa: Plan, X, Y, pl: Plan, B, Xs, nrhs: int, stream=None):
+    """Y = A X on the SpMV plan pa and L Xs = B on the SpTRSV plan pl in one launch
+    (row-major [n][nrhs] CUDA tensors of one dtype)."""
+    px, dx = _mat(X, pa.n_cols, nrhs, "X")
+    py, dy = _mat(Y, pa.n_rows, nrhs, "Y")
+    pb, db = _mat(B, pl.n_rows, nrhs, "B")
+    ps, ds = _mat(Xs, pl.n_rows, nrhs, "Xs")
+    if len({dx, dy, db, ds}) != 1:
+        raise ValueError("X, Y, B and Xs must have the same dtype")
+    _check(lib().ddf_batch_run(pa.handle, px, py, pl.handle, pb, ps, int(nrhs), dx, _stream(stream)),
+           "ddf_batch_run")
 
 
 def ddf_tune(plan: Plan, inp, out, nrhs: int, stream=None) -> int:

@@ -14,6 +14,7 @@
 // a butterfly over the groups, a fixed order, so results do not depend on
 // timing.  A row's points (value, column) are read 32 at a time, lane t
 // loading point t, and handed to the groups with shuffles.
+#include <initializer_list>
 #include <vector>
 
 #include "ddf_internal.cuh"
@@ -286,51 +287,60 @@ __device__ __forceinline__ void spmm_row_extent(const dcod& C, int32_t i0, int32
     }
 }
 
-// One warp per work unit.  Element-per-lane layout: rows in pairs, the next
-// row's points loading while the current row's X rows are read.  16-byte
-// layout: G rows at a time, one per lane group when all have at most
+// Operands of the multi-RHS SpMV: the plan's codelets, rows (starts, col),
+// values, work units and value tiles, and the blocks X and Y.
+template <typename TV, typename TX>
+struct MulArgs {
+    const dcod* cod;
+    const int32_t* st;
+    const int32_t* col;
+    const TV* val;
+    const TX* X;
+    TX* Y;
+    int32_t nrhs;
+    const dunit* units[3];
+    int64_t nunits[3];
+    const dtile* tiles[2];
+    int64_t ntiles[2];
+};
+
+// One work unit on one warp.  Element-per-lane layout: rows in pairs, the
+// next row's points loading while the current row's X rows are read.
+// 16-byte layout: G rows at a time, one per lane group when all have at most
 // SHORT_ROW points, else one after another on the whole warp.
 template <typename TV, typename TX, class LY>
-__global__ void __launch_bounds__(DDF_CTA_THREADS)
-k_spmm(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64_t nunits,
-       const int32_t* __restrict__ st, const int32_t* __restrict__ col, const TV* __restrict__ val,
-       const TX* __restrict__ X, TX* __restrict__ Y, int32_t nrhs) {
+__device__ __forceinline__ void spmm_unit(const MulArgs<TV, TX>& A, const dunit& U, int lane) {
     constexpr int G = LY::G, LP = LY::LP;
-    const int lane = threadIdx.x & 31;
     const int g = lane / LP, c = lane % LP;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nunits; u += nw) {
-        const dunit U = units[u];
-        const int32_t c0 = U.cod;
-        const int32_t ncods = U.i0b < 0 ? -U.i0b : 1;
-        for (int32_t k = 0; k < ncods; ++k) {
-            const dcod C = cod[c0 + k];
-            const int32_t b0 = U.i0b < 0 ? 0 : U.i0b;
-            const int32_t e0 = U.i0b < 0 ? C.m : U.i0e;
-            if constexpr (LP == 32) {
-                SRow<TX> ma, mb;
-                srow_load<TV, TX>(C, b0, b0 < e0, st, col, val, lane, 1, -1, ma);
-                for (int32_t i0 = b0; i0 < e0; i0 += 2) {
-                    srow_load<TV, TX>(C, i0 + 1, i0 + 1 < e0, st, col, val, lane, 1, -1, mb);
-                    srow_compute<TV, TX, LY>(C, i0, ma, col, val, X, Y, nrhs, lane);
-                    if (i0 + 1 >= e0) break;
-                    srow_load<TV, TX>(C, i0 + 2, i0 + 2 < e0, st, col, val, lane, 1, -1, ma);
-                    srow_compute<TV, TX, LY>(C, i0 + 1, mb, col, val, X, Y, nrhs, lane);
-                }
-            } else {
-                for (int32_t i0 = b0; i0 < e0; i0 += G) {
-                    const int32_t i = i0 + g;
-                    int32_t kb = 0, L = 0;
-                    if (i < e0) spmm_row_extent(C, i, -1, st, kb, L);
-                    if (!__any_sync(0xffffffffu, L > SHORT_ROW)) {
-                        if (i < e0)
-                            gspmm_row<TV, TX, LY>(C, i, kb, L, 1, C.f0 + C.rho * i, col, val, X, Y, nrhs, g, c);
-                    } else {
-                        for (int32_t h = i0; h < min(i0 + G, e0); ++h) {
-                            SRow<TX> m;
-                            srow_load<TV, TX>(C, h, true, st, col, val, lane, 1, -1, m);
-                            srow_compute<TV, TX, LY>(C, h, m, col, val, X, Y, nrhs, lane);
-                        }
+    const int32_t ncods = U.i0b < 0 ? -U.i0b : 1;
+    for (int32_t k = 0; k < ncods; ++k) {
+        const dcod C = A.cod[U.cod + k];
+        const int32_t b0 = U.i0b < 0 ? 0 : U.i0b;
+        const int32_t e0 = U.i0b < 0 ? C.m : U.i0e;
+        if constexpr (LP == 32) {
+            SRow<TX> ma, mb;
+            srow_load<TV, TX>(C, b0, b0 < e0, A.st, A.col, A.val, lane, 1, -1, ma);
+            for (int32_t i0 = b0; i0 < e0; i0 += 2) {
+                srow_load<TV, TX>(C, i0 + 1, i0 + 1 < e0, A.st, A.col, A.val, lane, 1, -1, mb);
+                srow_compute<TV, TX, LY>(C, i0, ma, A.col, A.val, A.X, A.Y, A.nrhs, lane);
+                if (i0 + 1 >= e0) break;
+                srow_load<TV, TX>(C, i0 + 2, i0 + 2 < e0, A.st, A.col, A.val, lane, 1, -1, ma);
+                srow_compute<TV, TX, LY>(C, i0 + 1, mb, A.col, A.val, A.X, A.Y, A.nrhs, lane);
+            }
+        } else {
+            for (int32_t i0 = b0; i0 < e0; i0 += G) {
+                const int32_t i = i0 + g;
+                int32_t kb = 0, L = 0;
+                if (i < e0) spmm_row_extent(C, i, -1, A.st, kb, L);
+                if (!__any_sync(0xffffffffu, L > SHORT_ROW)) {
+                    if (i < e0)
+                        gspmm_row<TV, TX, LY>(C, i, kb, L, 1, C.f0 + C.rho * i, A.col, A.val, A.X, A.Y, A.nrhs, g,
+                                              c);
+                } else {
+                    for (int32_t h = i0; h < min(i0 + G, e0); ++h) {
+                        SRow<TX> m;
+                        srow_load<TV, TX>(C, h, true, A.st, A.col, A.val, lane, 1, -1, m);
+                        srow_compute<TV, TX, LY>(C, h, m, A.col, A.val, A.X, A.Y, A.nrhs, lane);
                     }
                 }
             }
@@ -338,57 +348,62 @@ k_spmm(const dcod* __restrict__ cod, const dunit* __restrict__ units, int64_t nu
     }
 }
 
-// Rows of SpMV value tiles (point-major values), one warp per tile, rows laid
-// out over the lanes as in k_spmm.
+// One value tile (point-major values of up to 8 rows) on one warp, rows laid
+// out over the lanes as in spmm_unit.
 template <typename TV, typename TX, class LY>
-__global__ void __launch_bounds__(DDF_CTA_THREADS)
-k_spmm_tile(const dcod* __restrict__ cod, const dtile* __restrict__ tiles, int64_t ntiles,
-            const int32_t* __restrict__ st, const int32_t* __restrict__ col, const TV* __restrict__ val,
-            const TX* __restrict__ X, TX* __restrict__ Y, int32_t nrhs) {
+__device__ __forceinline__ void spmm_tile(const MulArgs<TV, TX>& A, const dtile& T, int lane) {
     constexpr int G = LY::G, LP = LY::LP;
-    const int lane = threadIdx.x & 31;
     const int g = lane / LP, c = lane % LP;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles; t += nw) {
-        const dtile T = tiles[t];
-        const int32_t w = (int32_t)(T.meta & 7u) + 1;
-        auto codelet = [&](int32_t r) { return cod[T.cod + (int32_t)((T.meta >> (3 + 3 * r)) & 7u)]; };
-        if constexpr (LP == 32) {
-            SRow<TX> ma, mb;
-            dcod Ca = codelet(0), Cb = Ca;
-            srow_load<TV, TX>(Ca, T.q - Ca.q0, true, st, col, val, lane, w, T.vb, ma);
-            for (int32_t r = 0; r < w; r += 2) {
-                if (r + 1 < w) {
-                    Cb = codelet(r + 1);
-                    srow_load<TV, TX>(Cb, T.q + r + 1 - Cb.q0, true, st, col, val, lane, w, T.vb + r + 1, mb);
-                }
-                srow_compute<TV, TX, LY>(Ca, T.q + r - Ca.q0, ma, col, val, X, Y, nrhs, lane);
-                if (r + 1 >= w) break;
-                if (r + 2 < w) {
-                    Ca = codelet(r + 2);
-                    srow_load<TV, TX>(Ca, T.q + r + 2 - Ca.q0, true, st, col, val, lane, w, T.vb + r + 2, ma);
-                }
-                srow_compute<TV, TX, LY>(Cb, T.q + r + 1 - Cb.q0, mb, col, val, X, Y, nrhs, lane);
+    const int32_t w = (int32_t)(T.meta & 7u) + 1;
+    auto codelet = [&](int32_t r) { return A.cod[T.cod + (int32_t)((T.meta >> (3 + 3 * r)) & 7u)]; };
+    if constexpr (LP == 32) {
+        SRow<TX> ma, mb;
+        dcod Ca = codelet(0), Cb = Ca;
+        srow_load<TV, TX>(Ca, T.q - Ca.q0, true, A.st, A.col, A.val, lane, w, T.vb, ma);
+        for (int32_t r = 0; r < w; r += 2) {
+            if (r + 1 < w) {
+                Cb = codelet(r + 1);
+                srow_load<TV, TX>(Cb, T.q + r + 1 - Cb.q0, true, A.st, A.col, A.val, lane, w, T.vb + r + 1, mb);
             }
-        } else {
-            for (int32_t r0 = 0; r0 < w; r0 += G) {
-                const int32_t r = r0 + g;
-                dcod C = codelet(min(r, w - 1));
-                const int32_t i = T.q + r - C.q0;
-                const int32_t L = r < w ? C.n : 0;   // tile rows are BLAS / PSC I rows of C.n points
-                if (!__any_sync(0xffffffffu, L > SHORT_ROW)) {
-                    if (r < w)
-                        gspmm_row<TV, TX, LY>(C, i, T.vb + r, L, w, C.f0 + C.rho * i, col, val, X, Y, nrhs, g, c);
-                } else {
-                    for (int32_t h = r0; h < min(r0 + G, w); ++h) {
-                        const dcod Ch = codelet(h);
-                        SRow<TX> m;
-                        srow_load<TV, TX>(Ch, T.q + h - Ch.q0, true, st, col, val, lane, w, T.vb + h, m);
-                        srow_compute<TV, TX, LY>(Ch, T.q + h - Ch.q0, m, col, val, X, Y, nrhs, lane);
-                    }
+            srow_compute<TV, TX, LY>(Ca, T.q + r - Ca.q0, ma, A.col, A.val, A.X, A.Y, A.nrhs, lane);
+            if (r + 1 >= w) break;
+            if (r + 2 < w) {
+                Ca = codelet(r + 2);
+                srow_load<TV, TX>(Ca, T.q + r + 2 - Ca.q0, true, A.st, A.col, A.val, lane, w, T.vb + r + 2, ma);
+            }
+            srow_compute<TV, TX, LY>(Cb, T.q + r + 1 - Cb.q0, mb, A.col, A.val, A.X, A.Y, A.nrhs, lane);
+        }
+    } else {
+        for (int32_t r0 = 0; r0 < w; r0 += G) {
+            const int32_t r = r0 + g;
+            const dcod C = codelet(min(r, w - 1));
+            const int32_t i = T.q + r - C.q0;
+            const int32_t L = r < w ? C.n : 0;   // tile rows are BLAS / PSC I rows of C.n points
+            if (!__any_sync(0xffffffffu, L > SHORT_ROW)) {
+                if (r < w)
+                    gspmm_row<TV, TX, LY>(C, i, T.vb + r, L, w, C.f0 + C.rho * i, A.col, A.val, A.X, A.Y, A.nrhs, g,
+                                          c);
+            } else {
+                for (int32_t h = r0; h < min(r0 + G, w); ++h) {
+                    const dcod Ch = codelet(h);
+                    SRow<TX> m;
+                    srow_load<TV, TX>(Ch, T.q + h - Ch.q0, true, A.st, A.col, A.val, lane, w, T.vb + h, m);
+                    srow_compute<TV, TX, LY>(Ch, T.q + h - Ch.q0, m, A.col, A.val, A.X, A.Y, A.nrhs, lane);
                 }
             }
         }
+    }
+}
+
+// Work unit array k (k < 3) or tile array k - 3 of the plan, one warp per item.
+template <typename TV, typename TX, class LY>
+__global__ void __launch_bounds__(DDF_CTA_THREADS) k_spmm(MulArgs<TV, TX> A, int k) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t count = k < 3 ? A.nunits[k] : A.ntiles[k - 3];
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < count; u += nw) {
+        if (k < 3) spmm_unit<TV, TX, LY>(A, A.units[k][u], lane);
+        else spmm_tile<TV, TX, LY>(A, A.tiles[k - 3][u], lane);
     }
 }
 
@@ -406,27 +421,54 @@ __global__ void k_fill_m(U* __restrict__ x, int64_t n, U pattern, uint32_t* __re
     for (int64_t i = i0; i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] = pattern;
 }
 
-template <typename TX>
-__device__ __noinline__ TX wait_m(const TX* p, int32_t* status, uint32_t* abort_flag, int64_t cap_ns) {
-    using B = RB<TX>;
-    uint64_t t0 = ddf_globaltimer();
-    uint32_t it = 0, ns = 32;
-    while (true) {
-        typename B::U v = B::ld(p);
-        if (v != B::SENT) return B::val(v);
-        ++it;
-        if (it > 16) {
-            __nanosleep(ns);
-            ns = min(ns * 2, 128u);
-        }
+// Waits until none of the loaded X entries xb[t] (points t < cnt) holds the
+// fill pattern: the X rows of every point still pending are read again, all
+// together, each round, so a row waits for its latest dependency plus one
+// round trip rather than for each pending point in turn.  Bounded: after
+// cap_ns (or once another warp gave up) the pending entries become NaN and
+// the status word records DDF_ERR_TIMEOUT.
+template <class V, typename TX, int NB, int VEC>
+__device__ __forceinline__ void settle(typename V::U (&xb)[NB][VEC], const int32_t (&jv)[NB], int32_t cnt,
+                                       const TX* X, int32_t nrhs, int c, int32_t* status, uint32_t* abort_flag,
+                                       int64_t cap_ns) {
+    using RBx = RB<TX>;
+    uint32_t pend = 0;
+#pragma unroll
+    for (int t = 0; t < NB; ++t)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v)
+            if (t < cnt && xb[t][v] == RBx::SENT) pend |= 1u << t;
+    if (!pend) return;
+    const uint64_t t0 = ddf_globaltimer();
+    for (uint32_t it = 1;; ++it) {
+#pragma unroll
+        for (int t = 0; t < NB; ++t)
+            if ((pend >> t) & 1u) V::ld_relaxed(X + (int64_t)jv[t] * nrhs + c * VEC, xb[t]);
+        uint32_t still = 0;
+#pragma unroll
+        for (int t = 0; t < NB; ++t)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v)
+                if (((pend >> t) & 1u) && xb[t][v] == RBx::SENT) still |= 1u << t;
+        pend = still;
+        if (!pend) return;
         if ((it & 15u) == 0) {
-            if (ddf_ld_relaxed_s32(abort_flag) != 0) return B::val(B::CANON);
-            if ((int64_t)(ddf_globaltimer() - t0) > cap_ns) {
+            bool give_up = ddf_ld_relaxed_s32(abort_flag) != 0;
+            if (!give_up && (int64_t)(ddf_globaltimer() - t0) > cap_ns) {
                 ddf_set_status(status, DDF_ERR_TIMEOUT);
                 atomicExch(abort_flag, 1u);
-                return B::val(B::CANON);
+                give_up = true;
+            }
+            if (give_up) {
+#pragma unroll
+                for (int t = 0; t < NB; ++t)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v)
+                        if (((pend >> t) & 1u) && xb[t][v] == RBx::SENT) xb[t][v] = RBx::CANON;
+                return;
             }
         }
+        if (it > 8) __nanosleep(64);
     }
 }
 
@@ -510,29 +552,13 @@ __device__ __forceinline__ void qrow_solve(const QRow<TX, LY::VEC>& m, const int
                 }
             }
             if (on) {
+                // the sub-block's points held by this lane: t = s0 + k G + g < cnt
+                const int32_t mine = cnt > s0 + g ? (cnt - s0 - g + G - 1) / G : 0;
+                settle<V, TX, NL, VEC>(xb, jv, mine, X, nrhs, c, status, abort_flag, cap_ns);
 #pragma unroll
-                for (int k = 0; k < NL; ++k) {
-                    if (s0 + k * G + g >= cnt) continue;
-                    TX* xr = X + (int64_t)jv[k] * nrhs + c * VEC;
-                    if constexpr (VEC > 1) {
-                        // the VEC elements were written together: wait for the first one
-                        // still pending, then read all of them again
-                        int pend = -1;
+                for (int k = 0; k < NL; ++k)
 #pragma unroll
-                        for (int v = VEC - 1; v >= 0; --v)
-                            if (xb[k][v] == RBx::SENT) pend = v;
-                        if (pend >= 0) {
-                            (void)wait_m<TX>(xr + pend, status, abort_flag, cap_ns);
-                            V::ld_relaxed(xr, xb[k]);
-                        }
-                    }
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) {
-                        const TX xj = (xb[k][v] != RBx::SENT) ? RBx::val(xb[k][v])
-                                                              : wait_m<TX>(xr + v, status, abort_flag, cap_ns);
-                        acc[v] += av[k] * xj;
-                    }
-                }
+                    for (int v = 0; v < VEC; ++v) acc[v] += av[k] * RBx::val(xb[k][v]);
             }
         }
         pv = npv;
@@ -618,25 +644,11 @@ __device__ __forceinline__ void grow_solve(const QRow<TX, LY::VEC>& m, const int
                 for (int v = 0; v < VEC; ++v) xb[t][v] = (U)0;
             }
         }
+        settle<V, TX, NB, VEC>(xb, jv, cnt, X, nrhs, c, status, abort_flag, cap_ns);
 #pragma unroll
-        for (int t = 0; t < NB; ++t) {
-            if (t >= cnt) break;
-            TX* xr = X + (int64_t)jv[t] * nrhs + c * VEC;
-            int pend = -1;
+        for (int t = 0; t < NB; ++t)
 #pragma unroll
-            for (int v = VEC - 1; v >= 0; --v)
-                if (xb[t][v] == RBx::SENT) pend = v;
-            if (pend >= 0) {   // written together: wait for the first pending element, read all again
-                (void)wait_m<TX>(xr + pend, status, abort_flag, cap_ns);
-                V::ld_relaxed(xr, xb[t]);
-            }
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                const TX xj = (xb[t][v] != RBx::SENT) ? RBx::val(xb[t][v])
-                                                      : wait_m<TX>(xr + v, status, abort_flag, cap_ns);
-                acc[v] += av[t] * xj;
-            }
-        }
+            for (int v = 0; v < VEC; ++v) acc[v] += av[t] * RBx::val(xb[t][v]);
     }
     U bits[VEC];
 #pragma unroll
@@ -647,87 +659,143 @@ __device__ __forceinline__ void grow_solve(const QRow<TX, LY::VEC>& m, const int
     V::st_relaxed(X + (int64_t)m.r * nrhs + c * VEC, bits);
 }
 
-// Multi-RHS forward substitution over the level-ordered plan.  A persistent
-// grid of warps takes the SpTRSV plan's work units (rows of one codelet, so
-// of one level: they never read one another) from a ticket, each warp on its
-// own, upt consecutive units per ticket (ddf_tune picks upt).  A warp holding
-// unit u waits only on rows of units before u, which running warps hold or
-// have finished, so the lowest unfinished unit can always proceed (no
-// co-residency needed, no cooperative launch).  Inside a unit, G rows at a
+constexpr int SPTRSM_MIN_CTAS = 2;   // resident CTAs per SM the register budget is cut for
+
+// Operands of the multi-RHS solve: the plan's level-ordered rows (unit
+// starts, seq, starts, col, values, 1 / L_rr), the blocks B and X, the ticket
+// (ticket[0]; ticket[1] is the give-up flag), the status word and the wait
+// limit.
+template <typename TV, typename TX>
+struct SolveArgs {
+    int32_t n;
+    int64_t nunits;
+    int32_t upt;
+    const int32_t* unit_q;
+    const int32_t* seq;
+    const int32_t* st;
+    const int32_t* col;
+    const TV* val;
+    const TX* dinv;
+    const TX* B;
+    TX* X;
+    int32_t nrhs;
+    uint32_t* ticket;
+    int32_t* status;
+    int64_t cap_ns;
+};
+
+// Units u0 .. u1 - 1 of the solve on one warp, in order.  Inside a unit (rows
+// of one codelet, so of one level: they never read one another), G rows at a
 // time: when all of them have at most SHORT_ROW points, one row per lane
 // group; otherwise one row after another on the whole warp, the G groups
 // splitting each row's points.  The next rows' data load while the current
-// ones are solved, and the next ticket is taken before the current units
-// start.  Row x[r] is ready once its elements no longer hold the fill
-// pattern; each lane waits on its own elements.
+// ones are solved.  Row x[r] is ready once its elements no longer hold the
+// fill pattern; each lane waits on its own elements.
 template <typename TV, typename TX, class LY>
-__global__ void __launch_bounds__(DDF_CTA_THREADS)
-k_sptrsm(int32_t n, int64_t nunits, int32_t upt, const int32_t* __restrict__ unit_q,
-         const int32_t* __restrict__ seq, const int32_t* __restrict__ st, const int32_t* __restrict__ col,
-         const TV* __restrict__ val,
-         const TX* __restrict__ dinv, const TX* __restrict__ B, TX* X, int32_t nrhs, uint32_t* ticket,
-         int32_t* status, int64_t cap_ns) {
+__device__ __forceinline__ void solve_units(const SolveArgs<TV, TX>& A, int64_t u0, int64_t u1, int lane) {
     constexpr int G = LY::G, LP = LY::LP, VEC = LY::VEC;
-    uint32_t* abort_flag = ticket + 1;
-    const int lane = threadIdx.x & 31;
     const int g = lane / LP, c = lane % LP;
-    auto take = [&]() -> int64_t {
-        uint32_t t = 0;
-        if (lane == 0) t = atomicAdd(ticket, 1u);
-        return (int64_t)__shfl_sync(0xffffffffu, t, 0);
-    };
-    int64_t t = take();
-    while (t * upt < nunits) {
-        const int64_t t_next = take();
-        const int64_t u1 = min(t * upt + upt, nunits);
-        for (int64_t u = t * upt; u < u1; ++u) {   // units in order: each one's rows share a level
-            const int64_t qa = unit_q[u];
-            const int64_t qz = (u + 1 < nunits) ? (int64_t)unit_q[u + 1] : (int64_t)n;
-            if constexpr (LP == 32) {
-                // one element per lane: rows one after another, points split over the warp
-                QRow<TX, VEC> ma, mb;
-                int64_t q = qa;
-                qrow_load<TV, TX, LY>(q, q < qz, seq, st, col, val, dinv, B, nrhs, lane, ma);
-                for (; q < qz; q += 2) {
-                    qrow_load<TV, TX, LY>(q + 1, q + 1 < qz, seq, st, col, val, dinv, B, nrhs, lane, mb);
-                    qrow_solve<TV, TX, LY>(ma, col, val, X, nrhs, lane, status, abort_flag, cap_ns);
-                    if (q + 1 >= qz) break;
-                    qrow_load<TV, TX, LY>(q + 2, q + 2 < qz, seq, st, col, val, dinv, B, nrhs, lane, ma);
-                    qrow_solve<TV, TX, LY>(mb, col, val, X, nrhs, lane, status, abort_flag, cap_ns);
-                }
-            } else {
-                QRow<TX, VEC> cur, nxt;
-                grow_load<TV, TX, LY>(qa + g, qa + g < qz, seq, st, col, val, dinv, B, nrhs, c, cur);
-                for (int64_t s0 = qa; s0 < qz; s0 += G) {
-                    grow_load<TV, TX, LY>(s0 + G + g, s0 + G + g < qz, seq, st, col, val, dinv, B, nrhs, c,
-                                          nxt);
-                    if (!__any_sync(0xffffffffu, cur.L > SHORT_ROW)) {
-                        if (s0 + g < qz)
-                            grow_solve<TV, TX, LY>(cur, col, val, X, nrhs, g, c, status, abort_flag, cap_ns);
-                    } else {
-                        // the G rows in order on the whole warp; row h's data comes from group h
-                        for (int h = 0; h < G; ++h) {
-                            if (s0 + h >= qz) break;
-                            QRow<TX, VEC> m;
-                            const int src = h * LP + c;
-                            m.r = __shfl_sync(0xffffffffu, cur.r, src);
-                            m.kb = __shfl_sync(0xffffffffu, cur.kb, src);
-                            m.L = __shfl_sync(0xffffffffu, cur.L, src);
-                            m.di = __shfl_sync(0xffffffffu, cur.di, src);
-#pragma unroll
-                            for (int v = 0; v < VEC; ++v) m.bv[v] = __shfl_sync(0xffffffffu, cur.bv[v], src);
-                            m.pv = (TX)0;
-                            m.pj = 0;
-                            if (lane < m.L) {
-                                m.pv = ddf_cvt<TX>(val[m.kb + lane]);
-                                m.pj = col[m.kb + lane];
-                            }
-                            qrow_solve<TV, TX, LY>(m, col, val, X, nrhs, lane, status, abort_flag, cap_ns);
-                        }
-                    }
-                    cur = nxt;
-                }
+    uint32_t* abort_flag = A.ticket + 1;
+    for (int64_t u = u0; u < u1; ++u) {
+        const int64_t qa = A.unit_q[u];
+        const int64_t qz = (u + 1 < A.nunits) ? (int64_t)A.unit_q[u + 1] : (int64_t)A.n;
+        if constexpr (LP == 32) {
+            // one element per lane: rows one after another, points split over the warp
+            QRow<TX, VEC> ma, mb;
+            int64_t q = qa;
+            qrow_load<TV, TX, LY>(q, q < qz, A.seq, A.st, A.col, A.val, A.dinv, A.B, A.nrhs, lane, ma);
+            for (; q < qz; q += 2) {
+                qrow_load<TV, TX, LY>(q + 1, q + 1 < qz, A.seq, A.st, A.col, A.val, A.dinv, A.B, A.nrhs, lane, mb);
+                qrow_solve<TV, TX, LY>(ma, A.col, A.val, A.X, A.nrhs, lane, A.status, abort_flag, A.cap_ns);
+                if (q + 1 >= qz) break;
+                qrow_load<TV, TX, LY>(q + 2, q + 2 < qz, A.seq, A.st, A.col, A.val, A.dinv, A.B, A.nrhs, lane, ma);
+                qrow_solve<TV, TX, LY>(mb, A.col, A.val, A.X, A.nrhs, lane, A.status, abort_flag, A.cap_ns);
             }
+        } else {
+            QRow<TX, VEC> cur, nxt;
+            grow_load<TV, TX, LY>(qa + g, qa + g < qz, A.seq, A.st, A.col, A.val, A.dinv, A.B, A.nrhs, c, cur);
+            for (int64_t s0 = qa; s0 < qz; s0 += G) {
+                grow_load<TV, TX, LY>(s0 + G + g, s0 + G + g < qz, A.seq, A.st, A.col, A.val, A.dinv, A.B, A.nrhs,
+                                      c, nxt);
+                if (!__any_sync(0xffffffffu, cur.L > SHORT_ROW)) {
+                    if (s0 + g < qz)
+                        grow_solve<TV, TX, LY>(cur, A.col, A.val, A.X, A.nrhs, g, c, A.status, abort_flag, A.cap_ns);
+                } else {
+                    // the G rows in order on the whole warp; row h's data comes from group h
+                    for (int h = 0; h < G; ++h) {
+                        if (s0 + h >= qz) break;
+                        QRow<TX, VEC> m;
+                        const int src = h * LP + c;
+                        m.r = __shfl_sync(0xffffffffu, cur.r, src);
+                        m.kb = __shfl_sync(0xffffffffu, cur.kb, src);
+                        m.L = __shfl_sync(0xffffffffu, cur.L, src);
+                        m.di = __shfl_sync(0xffffffffu, cur.di, src);
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) m.bv[v] = __shfl_sync(0xffffffffu, cur.bv[v], src);
+                        m.pv = (TX)0;
+                        m.pj = 0;
+                        if (lane < m.L) {
+                            m.pv = ddf_cvt<TX>(A.val[m.kb + lane]);
+                            m.pj = A.col[m.kb + lane];
+                        }
+                        qrow_solve<TV, TX, LY>(m, A.col, A.val, A.X, A.nrhs, lane, A.status, abort_flag, A.cap_ns);
+                    }
+                }
+                cur = nxt;
+            }
+        }
+    }
+}
+
+// A warp's ticket, taken by lane 0 and shared with the warp.
+__device__ __forceinline__ int64_t take_ticket(uint32_t* ticket, int lane) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(ticket, 1u);
+    return (int64_t)__shfl_sync(0xffffffffu, t, 0);
+}
+
+// Multi-RHS forward substitution over the level-ordered plan.  A persistent
+// grid of warps takes the SpTRSV plan's work units from a ticket, each warp
+// on its own, upt consecutive units per ticket (ddf_tune picks upt).  A warp
+// holding unit u waits only on rows of units before u, which running warps
+// hold or have finished, so the lowest unfinished unit can always proceed
+// (no co-residency needed, no cooperative launch).  The next ticket is taken
+// before the current units start.
+template <typename TV, typename TX, class LY>
+__global__ void __launch_bounds__(DDF_CTA_THREADS, SPTRSM_MIN_CTAS) k_sptrsm(SolveArgs<TV, TX> A) {
+    const int lane = threadIdx.x & 31;
+    int64_t t = take_ticket(A.ticket, lane);
+    while (t * A.upt < A.nunits) {
+        const int64_t t_next = take_ticket(A.ticket, lane);
+        solve_units<TV, TX, LY>(A, t * A.upt, min(t * A.upt + A.upt, A.nunits), lane);
+        t = t_next;
+    }
+}
+
+// A batch's SpMV and SpTRSV in one launch: the tickets first hand out the
+// solve's units (as in k_sptrsm), then the SpMV's work items (its three unit
+// arrays, then its two tile arrays), one item per ticket.  SpMV items wait on
+// nothing, so the argument of k_sptrsm still holds, and warps that find no
+// solve unit left run the products while the solve's deep levels finish.
+template <typename TV, typename TX, class LY>
+__global__ void __launch_bounds__(DDF_CTA_THREADS, SPTRSM_MIN_CTAS)
+k_batch(SolveArgs<TV, TX> S, MulArgs<TV, TX> M) {
+    const int lane = threadIdx.x & 31;
+    const int64_t ts = (S.nunits + S.upt - 1) / S.upt;
+    const int64_t c0 = M.nunits[0], c1 = c0 + M.nunits[1], c2 = c1 + M.nunits[2];
+    const int64_t c3 = c2 + M.ntiles[0], c4 = c3 + M.ntiles[1];
+    int64_t t = take_ticket(S.ticket, lane);
+    while (t < ts + c4) {
+        const int64_t t_next = take_ticket(S.ticket, lane);
+        if (t < ts) {
+            solve_units<TV, TX, LY>(S, t * S.upt, min(t * S.upt + S.upt, S.nunits), lane);
+        } else {
+            const int64_t i = t - ts;
+            if (i < c0) spmm_unit<TV, TX, LY>(M, M.units[0][i], lane);
+            else if (i < c1) spmm_unit<TV, TX, LY>(M, M.units[1][i - c0], lane);
+            else if (i < c2) spmm_unit<TV, TX, LY>(M, M.units[2][i - c1], lane);
+            else if (i < c3) spmm_tile<TV, TX, LY>(M, M.tiles[0][i - c2], lane);
+            else spmm_tile<TV, TX, LY>(M, M.tiles[1][i - c3], lane);
         }
         t = t_next;
     }
@@ -740,96 +808,164 @@ unsigned grid_units(int64_t nunits, int sm) {
 }
 
 // Lanes per row of X for the 16-byte form (nrhs = VEC * LP, LP a power of two
-// from 2 to 16, blocks 16-byte aligned), else 0 (one element per lane).
+// from 2 to 16, every block 16-byte aligned), else 0 (one element per lane).
 template <typename TX>
-int vector_lp(int32_t nrhs, const void* a, const void* b) {
+int vector_lp(int32_t nrhs, std::initializer_list<const void*> blocks) {
     constexpr int VEC = 16 / (int)sizeof(TX);
-    if (nrhs % VEC || ((uintptr_t)a & 15u) || ((uintptr_t)b & 15u)) return 0;
+    if (nrhs % VEC) return 0;
+    for (const void* b : blocks)
+        if ((uintptr_t)b & 15u) return 0;
     const int lp = nrhs / VEC;
     return (lp == 2 || lp == 4 || lp == 8 || (lp == 16 && VEC == 2)) ? lp : 0;
 }
 
-template <typename TV, typename TX, class LY>
-int launch_spmm_as(ddf_plan_s* p, const TV* val, const TX* X, TX* Y, int32_t nrhs, cudaStream_t s, int sm) {
-    int launches = 0;
-    for (int t = 0; t < 3; ++t) {
-        if (p->nunits[t] <= 0) continue;
-        k_spmm<TV, TX, LY><<<grid_units(p->nunits[t], sm), DDF_CTA_THREADS, 0, s>>>(
-            p->cod, p->units[t], p->nunits[t], p->starts, p->col, val, X, Y, nrhs);
-        ddf_count_launch();
-        ++launches;
+// Calls f with the lane layout for (nrhs, blocks): Lay<TX, VEC, LP> or the
+// one-element layout.
+template <typename TX, typename F>
+void with_layout(int32_t nrhs, std::initializer_list<const void*> blocks, F&& f) {
+    constexpr int VEC = 16 / (int)sizeof(TX);
+    switch (vector_lp<TX>(nrhs, blocks)) {
+        case 2: f(Lay<TX, VEC, 2>{}); break;
+        case 4: f(Lay<TX, VEC, 4>{}); break;
+        case 8: f(Lay<TX, VEC, 8>{}); break;
+        case 16:
+            if constexpr (VEC == 2) f(Lay<TX, VEC, 16>{});
+            break;
+        default: f(Lay<TX, 1, 32>{});
     }
-    for (int t = 0; t < 2; ++t) {
-        if (p->ntiles[t] <= 0) continue;
-        k_spmm_tile<TV, TX, LY><<<grid_units(p->ntiles[t], sm), DDF_CTA_THREADS, 0, s>>>(
-            p->cod, p->tiles[t], p->ntiles[t], p->starts, p->col, val, X, Y, nrhs);
-        ddf_count_launch();
-        ++launches;
+}
+
+template <typename TV, typename TX>
+MulArgs<TV, TX> mul_args(const ddf_plan_s* p, const TV* val, const TX* X, TX* Y, int32_t nrhs) {
+    MulArgs<TV, TX> A;
+    A.cod = p->cod;
+    A.st = p->starts;
+    A.col = p->col;
+    A.val = val;
+    A.X = X;
+    A.Y = Y;
+    A.nrhs = nrhs;
+    for (int k = 0; k < 3; ++k) {
+        A.units[k] = p->units[k];
+        A.nunits[k] = p->nunits[k];
     }
-    return launches;
+    for (int k = 0; k < 2; ++k) {
+        A.tiles[k] = p->tiles[k];
+        A.ntiles[k] = p->ntiles[k];
+    }
+    return A;
+}
+
+template <typename TV, typename TX>
+SolveArgs<TV, TX> solve_args(const ddf_plan_s* p, const TV* val, const TX* dinv, const TX* B, TX* X,
+                             int32_t nrhs) {
+    SolveArgs<TV, TX> A;
+    A.n = p->n;
+    A.nunits = p->nunits[0];
+    A.upt = p->mrhs_units_per_ticket > 0 ? p->mrhs_units_per_ticket : 1;
+    A.unit_q = p->unit_q;
+    A.seq = p->seq;
+    A.st = p->starts;
+    A.col = p->col;
+    A.val = val;
+    A.dinv = dinv;
+    A.B = B;
+    A.X = X;
+    A.nrhs = nrhs;
+    A.ticket = p->ticket;
+    A.status = p->status;
+    A.cap_ns = p->opts.spin_cap_ns;
+    return A;
 }
 
 template <typename TV, typename TX>
 ddf_status launch_spmm(ddf_plan_s* p, const TV* val, const TX* X, TX* Y, int32_t nrhs, cudaStream_t s) {
-    constexpr int VEC = 16 / (int)sizeof(TX);
     const int sm = p->sm_count > 0 ? p->sm_count : 152;
+    const MulArgs<TV, TX> A = mul_args<TV, TX>(p, val, X, Y, nrhs);
     int launches = 0;
-    switch (vector_lp<TX>(nrhs, X, Y)) {
-        case 2: launches = launch_spmm_as<TV, TX, Lay<TX, VEC, 2>>(p, val, X, Y, nrhs, s, sm); break;
-        case 4: launches = launch_spmm_as<TV, TX, Lay<TX, VEC, 4>>(p, val, X, Y, nrhs, s, sm); break;
-        case 8: launches = launch_spmm_as<TV, TX, Lay<TX, VEC, 8>>(p, val, X, Y, nrhs, s, sm); break;
-        case 16:
-            if constexpr (VEC == 2) launches = launch_spmm_as<TV, TX, Lay<TX, VEC, 16>>(p, val, X, Y, nrhs, s, sm);
-            break;
-        default: launches = launch_spmm_as<TV, TX, Lay<TX, 1, 32>>(p, val, X, Y, nrhs, s, sm);
-    }
+    with_layout<TX>(nrhs, {X, Y}, [&](auto ly) {
+        using LY = decltype(ly);
+        for (int k = 0; k < 5; ++k) {
+            const int64_t count = k < 3 ? A.nunits[k] : A.ntiles[k - 3];
+            if (count <= 0) continue;
+            k_spmm<TV, TX, LY><<<grid_units(count, sm), DDF_CTA_THREADS, 0, s>>>(A, k);
+            ddf_count_launch();
+            ++launches;
+        }
+    });
     p->last_launches = launches;
     DDF_CUDA_TRY(cudaGetLastError());
     return DDF_OK;
 }
 
-template <typename TV, typename TX, class LY>
-ddf_status launch_sptrsm_as(ddf_plan_s* p, const TV* val, const TX* dinv, const TX* B, TX* X, int32_t nrhs,
-                            cudaStream_t s, int sm) {
-    const auto kern = k_sptrsm<TV, TX, LY>;
+// Persistent grid of a ticket kernel: its resident CTAs, at most enough for
+// `tickets` warps.
+template <typename K>
+ddf_status ticket_grid(K kern, int64_t tickets, int sm, unsigned* ctas) {
     int per_sm = 0;
     DDF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, DDF_CTA_THREADS, 0));
-    const int32_t upt = p->mrhs_units_per_ticket > 0 ? p->mrhs_units_per_ticket : 1;
-    const int64_t tickets = (p->nunits[0] + upt - 1) / upt;
     const int64_t want = (tickets + DDF_WARPS_PER_CTA - 1) / DDF_WARPS_PER_CTA;
-    const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm * std::max(per_sm, 1)));
-    kern<<<(unsigned)ctas, DDF_CTA_THREADS, 0, s>>>(p->n, p->nunits[0], upt, p->unit_q, p->seq, p->starts, p->col,
-                                                   val, dinv, B, X, nrhs, p->ticket, p->status,
-                                                   p->opts.spin_cap_ns);
-    ddf_count_launch();
+    *ctas = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm * std::max(per_sm, 1)));
     return DDF_OK;
+}
+
+// X := the fill pattern and the plan's ticket and give-up flag := 0.
+template <typename TX>
+void fill_solve(ddf_plan_s* p, TX* X, int32_t nrhs, cudaStream_t s, int sm) {
+    using RBx = RB<TX>;
+    const int64_t ne = (int64_t)p->n * nrhs;
+    k_fill_m<typename RBx::U><<<ddf_grid(ne > 0 ? ne : 1, 256, (unsigned)sm * 8), 256, 0, s>>>(
+        (typename RBx::U*)X, ne, RBx::SENT, p->ticket);
+    ddf_count_launch();
 }
 
 template <typename TV, typename TX>
 ddf_status launch_sptrsm(ddf_plan_s* p, const TV* val, const TX* dinv, const TX* B, TX* X, int32_t nrhs,
                          cudaStream_t s) {
-    using RBx = RB<TX>;
-    constexpr int VEC = 16 / (int)sizeof(TX);
     const int sm = p->sm_count > 0 ? p->sm_count : 152;
-    const int64_t ne = (int64_t)p->n * nrhs;
-    k_fill_m<typename RBx::U><<<ddf_grid(ne > 0 ? ne : 1, 256, (unsigned)sm * 8), 256, 0, s>>>(
-        (typename RBx::U*)X, ne, RBx::SENT, p->ticket);
-    ddf_count_launch();
+    fill_solve<TX>(p, X, nrhs, s, sm);
     ddf_status st = DDF_OK;
     if (p->nunits[0] > 0) {
-        switch (vector_lp<TX>(nrhs, B, X)) {
-            case 2: st = launch_sptrsm_as<TV, TX, Lay<TX, VEC, 2>>(p, val, dinv, B, X, nrhs, s, sm); break;
-            case 4: st = launch_sptrsm_as<TV, TX, Lay<TX, VEC, 4>>(p, val, dinv, B, X, nrhs, s, sm); break;
-            case 8: st = launch_sptrsm_as<TV, TX, Lay<TX, VEC, 8>>(p, val, dinv, B, X, nrhs, s, sm); break;
-            case 16:
-                if constexpr (VEC == 2)
-                    st = launch_sptrsm_as<TV, TX, Lay<TX, VEC, 16>>(p, val, dinv, B, X, nrhs, s, sm);
-                break;
-            default: st = launch_sptrsm_as<TV, TX, Lay<TX, 1, 32>>(p, val, dinv, B, X, nrhs, s, sm);
-        }
+        const SolveArgs<TV, TX> A = solve_args<TV, TX>(p, val, dinv, B, X, nrhs);
+        with_layout<TX>(nrhs, {B, X}, [&](auto ly) {
+            using LY = decltype(ly);
+            unsigned ctas = 1;
+            st = ticket_grid(k_sptrsm<TV, TX, LY>, (A.nunits + A.upt - 1) / A.upt, sm, &ctas);
+            if (st) return;
+            k_sptrsm<TV, TX, LY><<<ctas, DDF_CTA_THREADS, 0, s>>>(A);
+            ddf_count_launch();
+        });
     }
     if (st) return st;
     p->last_launches = 2;
+    DDF_CUDA_TRY(cudaGetLastError());
+    return DDF_OK;
+}
+
+// Both executors of a batch in one launch (after the solve's fill).
+template <typename TV, typename TX>
+ddf_status launch_batch(ddf_plan_s* pa, const TV* va, const TX* X, TX* Y, ddf_plan_s* pl, const TV* vl,
+                        const TX* dinv, const TX* B, TX* Xs, int32_t nrhs, cudaStream_t s) {
+    const int sm = pl->sm_count > 0 ? pl->sm_count : 152;
+    fill_solve<TX>(pl, Xs, nrhs, s, sm);
+    const SolveArgs<TV, TX> S = solve_args<TV, TX>(pl, vl, dinv, B, Xs, nrhs);
+    const MulArgs<TV, TX> M = mul_args<TV, TX>(pa, va, X, Y, nrhs);
+    const int64_t tickets = (S.nunits + S.upt - 1) / S.upt + M.nunits[0] + M.nunits[1] + M.nunits[2] +
+                            M.ntiles[0] + M.ntiles[1];
+    ddf_status st = DDF_OK;
+    if (tickets > 0) {
+        with_layout<TX>(nrhs, {X, Y, B, Xs}, [&](auto ly) {
+            using LY = decltype(ly);
+            unsigned ctas = 1;
+            st = ticket_grid(k_batch<TV, TX, LY>, tickets, sm, &ctas);
+            if (st) return;
+            k_batch<TV, TX, LY><<<ctas, DDF_CTA_THREADS, 0, s>>>(S, M);
+            ddf_count_launch();
+        });
+    }
+    if (st) return st;
+    pa->last_launches = 0;
+    pl->last_launches = 2;
     DDF_CUDA_TRY(cudaGetLastError());
     return DDF_OK;
 }
@@ -843,6 +979,10 @@ ddf_status run_multi(ddf_plan_s* p, const void* in, void* out, int32_t nrhs, ddf
         return launch_sptrsm<double, double>(p, p->val, p->dinv, (const double*)in, (double*)out, nrhs, s);
     return launch_sptrsm<float, float>(p, (const float*)p->val_lp, p->dinv_lp, (const float*)in, (float*)out, nrhs,
                                        s);
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+    return na > 0 && nb > 0 && (const char*)a < (const char*)b + nb && (const char*)b < (const char*)a + na;
 }
 
 ddf_status check_multi(ddf_plan_s* p, const void* in, void* out, int32_t nrhs, ddf_dtype dtype) {
@@ -953,13 +1093,34 @@ ddf_status ddf_sptrsm(ddf_plan_t p, const void* B, void* X, int32_t nrhs, ddf_dt
     if (st) return st;
     if (p->kind != DDF_SPTRSV) return DDF_ERR_WRONG_KIND;
     const size_t bytes = (size_t)p->n * nrhs * (dtype == DDF_F64 ? 8 : 4);
-    if (p->n > 0 && (const char*)B < (const char*)X + bytes && (const char*)X < (const char*)B + bytes)
-        return DDF_ERR_ARG;
+    if (overlaps(B, bytes, X, bytes)) return DDF_ERR_ARG;
     if (p->n == 0) {
         p->last_launches = 0;
         return DDF_OK;
     }
     return run_multi(p, B, X, nrhs, dtype, (cudaStream_t)stream);
+}
+
+ddf_status ddf_batch_run(ddf_plan_t pa, const void* X, void* Y, ddf_plan_t pl, const void* B, void* Xs,
+                         int32_t nrhs, ddf_dtype dtype, ddf_stream_t stream) {
+    ddf_nvtx_range nvtx_("ddf_batch_run");
+    ddf_status st = check_multi(pa, X, Y, nrhs, dtype);
+    if (!st) st = check_multi(pl, B, Xs, nrhs, dtype);
+    if (st) return st;
+    if (pa->kind != DDF_SPMV || pl->kind != DDF_SPTRSV) return DDF_ERR_WRONG_KIND;
+    const size_t es = dtype == DDF_F64 ? 8 : 4;
+    const size_t nx = (size_t)pa->n_cols * nrhs * es, ny = (size_t)pa->n * nrhs * es;
+    const size_t ns = (size_t)pl->n * nrhs * es;
+    // the outputs Y and Xs are written while X, B (and each other) are read
+    if (overlaps(Xs, ns, B, ns) || overlaps(Xs, ns, X, nx) || overlaps(Xs, ns, Y, ny) || overlaps(Y, ny, X, nx) ||
+        overlaps(Y, ny, B, ns))
+        return DDF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == DDF_F64)
+        return launch_batch<double, double>(pa, pa->val, (const double*)X, (double*)Y, pl, pl->val, pl->dinv,
+                                            (const double*)B, (double*)Xs, nrhs, s);
+    return launch_batch<float, float>(pa, (const float*)pa->val_lp, (const float*)X, (float*)Y, pl,
+                                      (const float*)pl->val_lp, pl->dinv_lp, (const float*)B, (float*)Xs, nrhs, s);
 }
 
 ddf_status ddf_tune(ddf_plan_t p, const void* in, void* out, int32_t nrhs, ddf_dtype dtype, ddf_stream_t stream,

@@ -199,3 +199,101 @@ def test_multi_rhs_argument_errors(small_batch):
     with pytest.raises(ddf.DDFError) as e:
         ddf.ddf_inspect_batch([(bad.rowptr, bad.colidx, bad.values, 3)], ddf.DDF_SPTRSV)
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("nrhs", [32, 3])
+def test_sptrsm_wait_times_out_and_recovers(nrhs):
+    # Point the first off-diagonal entry of a row r at a row d that itself
+    # reads r: r waits for d and d for r, so the bounded waits must run out,
+    # latch DDF_ERR_TIMEOUT, leave NaN in X and the context usable.  nrhs 32
+    # runs the 16-byte lane layout, 3 the one-element layout.
+    lo = synth.random_pattern(3000, 3000, 0.003, 17, diag=True, lower=True)
+    o = ddf.ddf_opts_default(store_dtype=ddf.DDF_F32, spin_cap_ns=50_000_000)
+    q = ddf.ddf_inspect(dev(lo.rowptr), dev(lo.colidx), dev(lo.values), lo.n_cols, ddf.DDF_SPTRSV, o)
+    exp = ddf.ddf_plan_export(q)
+    seq, gs = exp["seq"], exp["gs"]
+    offl = np.diff(lo.rowptr) - 1
+    rows_of = np.repeat(np.arange(lo.n_rows), np.diff(lo.rowptr))
+    target = None
+    for pos in range(lo.n_rows):
+        row = int(seq[pos])
+        if offl[row] < 1:
+            continue
+        deps = rows_of[(lo.colidx == row) & (rows_of != row)]
+        if deps.size:
+            target = (int(gs[pos]), int(deps[0]))
+            break
+    assert target is not None
+    ddf.ddf_debug_set_dependency(q, *target)
+    B = np.random.default_rng(2).uniform(-1, 1, (lo.n_rows, nrhs)).astype(np.float32)
+    X = torch.zeros((lo.n_rows, nrhs), dtype=torch.float32, device="cuda")
+    ddf.ddf_sptrsm(q, dev(B), X, nrhs)
+    assert ddf.ddf_get_status(q) == 11
+    assert torch.isnan(X).any()
+    # the device is still usable: a clean plan solves to the FP32 bound
+    q2 = ddf.ddf_inspect(dev(lo.rowptr), dev(lo.colidx), dev(lo.values), lo.n_cols, ddf.DDF_SPTRSV,
+                         ddf.ddf_opts_default(store_dtype=ddf.DDF_F32))
+    ddf.ddf_sptrsm(q2, dev(B), X, nrhs)
+    assert ddf.ddf_get_status(q2) == 0
+    Xh = X.double().cpu().numpy()
+    for k in range(0, nrhs, 7):
+        bk = B[:, k].astype(np.float64)
+        assert np.linalg.norm(bk - oracle.spmv(lo, Xh[:, k])) <= 1e-5 * np.linalg.norm(bk)
+
+
+@pytest.mark.parametrize("nrhs,dt", [(32, torch.float32), (3, torch.float32), (8, torch.float64)])
+def test_batch_run_equals_separate_calls(small_batch, nrhs, dt):
+    # the one-launch form runs the same row computations as ddf_spmm and
+    # ddf_sptrsm, so its results are bit-identical; also recorded in a graph
+    lows = [synth.lower_triangle(m) for m in small_batch]
+    opts = {"store_dtype": ddf.DDF_F32} if dt == torch.float32 else {}
+    p = batch_plan(small_batch, ddf.DDF_SPMV, **opts)
+    q = batch_plan(lows, ddf.DDF_SPTRSV, **opts)
+    rng = np.random.default_rng(nrhs)
+    X = torch.from_numpy(rng.uniform(-1, 1, (p.n_cols, nrhs))).to(dt).cuda()
+    B = torch.from_numpy(rng.uniform(-1, 1, (q.n_rows, nrhs))).to(dt).cuda()
+    Y1 = torch.empty((p.n_rows, nrhs), dtype=dt, device="cuda")
+    X1 = torch.empty((q.n_rows, nrhs), dtype=dt, device="cuda")
+    ddf.ddf_spmm(p, X, Y1, nrhs)
+    ddf.ddf_sptrsm(q, B, X1, nrhs)
+    Y2 = torch.full_like(Y1, float("nan"))
+    X2 = torch.full_like(X1, float("nan"))
+    ddf.ddf_batch_run(p, X, Y2, q, B, X2, nrhs)
+    torch.cuda.synchronize()
+    assert ddf.ddf_get_status(q) == 0
+    assert torch.equal(Y1, Y2) and torch.equal(X1, X2)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            ddf.ddf_batch_run(p, X, Y2, q, B, X2, nrhs, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(2):
+        Y2.zero_()
+        X2.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(Y1, Y2) and torch.equal(X1, X2)
+    assert ddf.ddf_get_status(q) == 0
+
+
+def test_batch_run_argument_errors(small_batch):
+    lows = [synth.lower_triangle(m) for m in small_batch[:2]]
+    p = batch_plan(small_batch[:2], ddf.DDF_SPMV)
+    q = batch_plan(lows, ddf.DDF_SPTRSV)
+    X = torch.zeros((p.n_cols, 4), dtype=torch.float64, device="cuda")
+    Y = torch.zeros((p.n_rows, 4), dtype=torch.float64, device="cuda")
+    B = torch.zeros((q.n_rows, 4), dtype=torch.float64, device="cuda")
+    Xs = torch.zeros((q.n_rows, 4), dtype=torch.float64, device="cuda")
+    with pytest.raises(ddf.DDFError) as e:
+        ddf.ddf_batch_run(q, X, Y, p, B, Xs, 4)           # plans swapped
+    assert e.value.status == 8
+    with pytest.raises(ddf.DDFError) as e:
+        ddf.ddf_batch_run(p, X, Y, q, B, B, 4)            # Xs overlaps B
+    assert e.value.status == 1
+    with pytest.raises(ddf.DDFError) as e:
+        ddf.ddf_batch_run(p, X, Y, q, B, Y, 4)            # Xs overlaps Y
+    assert e.value.status == 1
+    ddf.ddf_batch_run(p, X, Y, q, B, Xs, 4)
+    assert ddf.ddf_get_status(q) == 0
