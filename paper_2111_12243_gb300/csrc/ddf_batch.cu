@@ -661,15 +661,17 @@ __device__ __forceinline__ void grow_solve(const QRow<TX, LY::VEC>& m, const int
 
 constexpr int SPTRSM_MIN_CTAS = 2;   // resident CTAs per SM the register budget is cut for
 
-// Operands of the multi-RHS solve: the plan's level-ordered rows (unit
-// starts, seq, starts, col, values, 1 / L_rr), the blocks B and X, the ticket
-// (ticket[0]; ticket[1] is the give-up flag), the status word and the wait
-// limit.
+// Operands of the multi-RHS solve: its work ranges (the plan's units, or for
+// a batch the units split where the matrix changes: first positions, and the
+// ticket order), the plan's level-ordered rows (seq, starts, col, values,
+// 1 / L_rr), the blocks B and X, the ticket (ticket[0]; ticket[1] is the
+// give-up flag), the status word and the wait limit.
 template <typename TV, typename TX>
 struct SolveArgs {
     int32_t n;
     int64_t nunits;
     int32_t upt;
+    const int32_t* order;   // units in ticket order (NULL: level order)
     const int32_t* unit_q;
     const int32_t* seq;
     const int32_t* st;
@@ -684,11 +686,11 @@ struct SolveArgs {
     int64_t cap_ns;
 };
 
-// Units u0 .. u1 - 1 of the solve on one warp, in order.  Inside a unit (rows
-// of one codelet, so of one level: they never read one another), G rows at a
-// time: when all of them have at most SHORT_ROW points, one row per lane
-// group; otherwise one row after another on the whole warp, the G groups
-// splitting each row's points.  The next rows' data load while the current
+// Ranges at ticket positions u0 .. u1 - 1 of the solve on one warp, in order.
+// Inside a range (rows of one codelet, so of one level: they never read one
+// another), G rows at a time: when all of them have at most SHORT_ROW
+// points, one row per lane group; otherwise one row after another on the
+// whole warp, the G groups splitting each row's points.  The next rows' data load while the current
 // ones are solved.  Row x[r] is ready once its elements no longer hold the
 // fill pattern; each lane waits on its own elements.
 template <typename TV, typename TX, class LY>
@@ -696,7 +698,8 @@ __device__ __forceinline__ void solve_units(const SolveArgs<TV, TX>& A, int64_t 
     constexpr int G = LY::G, LP = LY::LP, VEC = LY::VEC;
     const int g = lane / LP, c = lane % LP;
     uint32_t* abort_flag = A.ticket + 1;
-    for (int64_t u = u0; u < u1; ++u) {
+    for (int64_t i = u0; i < u1; ++i) {
+        const int64_t u = A.order ? (int64_t)A.order[i] : i;
         const int64_t qa = A.unit_q[u];
         const int64_t qz = (u + 1 < A.nunits) ? (int64_t)A.unit_q[u + 1] : (int64_t)A.n;
         if constexpr (LP == 32) {
@@ -801,6 +804,130 @@ k_batch(SolveArgs<TV, TX> S, MulArgs<TV, TX> M) {
     }
 }
 
+// Ticket order of a batch's solve.  In the block-diagonal plan, level l
+// holds the rows of every matrix at its own level l, so in plain level order
+// the deep matrices' last levels (few rows each, a chain of dependency hops)
+// run only after the shallow matrices' wide levels are done.  The solve's
+// work ranges are the plan's units split where the matrix changes (a codelet
+// may run across the end of one matrix's rows into the next one's); they
+// are sorted by normalized level, l / (depth of their matrix + 1), ties in
+// level order, which spreads every matrix over the whole run: the deep
+// chains advance beside the wide levels.  The order is topological: a
+// range's dependencies are rows of its own matrix at lower levels, whose
+// keys are no larger and which come first among equal keys.
+constexpr int ORDER_KEY_BITS = 20;
+
+__device__ __forceinline__ int32_t last_le(const int32_t* __restrict__ a, int32_t n, int32_t v) {
+    int32_t lo = 0, hi = n - 1;   // the last i with a[i] <= v (a[0] <= v)
+    while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (a[mid] <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// flag[q] = 1 where a range starts: a unit's first position, or a position
+// whose row belongs to another matrix than the row before it
+__global__ void k_range_flags(int32_t n, int64_t nu, const int32_t* __restrict__ unit_q,
+                              const int32_t* __restrict__ seq, const int32_t* __restrict__ moff, int32_t count,
+                              int32_t* __restrict__ flag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nu) flag[unit_q[i]] = 1;
+    if (i > 0 && i < n && last_le(moff, count, seq[i]) != last_le(moff, count, seq[i - 1])) flag[i] = 1;
+}
+
+__global__ void k_range_write(int32_t n, const int32_t* __restrict__ flag, const int64_t* __restrict__ off,
+                              int32_t* __restrict__ rq) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n && flag[q]) rq[off[q]] = (int32_t)q;
+}
+
+__global__ void k_range_level(int64_t nr, const int32_t* __restrict__ rq, const int32_t* __restrict__ seq,
+                              const int32_t* __restrict__ part_ptr, int32_t depth, const int32_t* __restrict__ moff,
+                              int32_t count, int32_t* __restrict__ rmat, int32_t* __restrict__ rlev,
+                              int32_t* __restrict__ mdepth) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nr) return;
+    const int32_t q = rq[r];
+    const int32_t m = last_le(moff, count, seq[q]);
+    const int32_t l = last_le(part_ptr, depth, q);
+    rmat[r] = m;
+    rlev[r] = l;
+    atomicMax(mdepth + m, l);
+}
+
+__global__ void k_range_key(int64_t nr, const int32_t* __restrict__ rmat, const int32_t* __restrict__ rlev,
+                            const int32_t* __restrict__ mdepth, uint32_t* __restrict__ key, int32_t* __restrict__ idx) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nr) return;
+    key[r] = (uint32_t)(((uint64_t)rlev[r] << ORDER_KEY_BITS) / ((uint64_t)mdepth[rmat[r]] + 1));
+    idx[r] = (int32_t)r;
+}
+
+// Builds p->mrhs_q / mrhs_order / mrhs_nr for a batch solve plan whose
+// matrices start at rows moff_h[0 .. count - 1].
+ddf_status build_mrhs_order(ddf_plan_s* p, const std::vector<int32_t>& moff_h, cudaStream_t s) {
+    const int64_t nu = p->nunits[0];
+    const int32_t n = p->n;
+    const int32_t count = (int32_t)moff_h.size();
+    if (nu < 1 || n < 2 || count < 2 || p->nblocks > 0) return DDF_OK;
+    int32_t *moff = nullptr, *flag = nullptr, *rq = nullptr, *rmat = nullptr, *rlev = nullptr, *mdepth = nullptr,
+            *idx = nullptr;
+    int64_t* off = nullptr;
+    uint32_t* key = nullptr;
+    int64_t nr = 0;
+    ddf_status st = ddf_alloc(&moff, count, s);
+    if (!st) st = ddf_alloc(&flag, n, s);
+    if (!st) st = ddf_alloc(&off, (int64_t)n + 1, s);
+    if (!st && cudaMemcpyAsync(moff, moff_h.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        st = DDF_ERR_CUDA;
+    if (!st && cudaMemsetAsync(flag, 0, sizeof(int32_t) * n, s) != cudaSuccess) st = DDF_ERR_CUDA;
+    if (!st) {
+        k_range_flags<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, nu, p->unit_q, p->seq, moff, count, flag);
+        ddf_count_launch();
+        if (cudaGetLastError() != cudaSuccess) st = DDF_ERR_CUDA;
+    }
+    if (!st) st = ddf_scan_i32_to_i64(flag, off, n, s);
+    if (!st && (cudaMemcpyAsync(&nr, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess))
+        st = DDF_ERR_CUDA;
+    if (!st) st = ddf_alloc(&rq, nr, s);
+    if (!st) st = ddf_alloc(&rmat, nr, s);
+    if (!st) st = ddf_alloc(&rlev, nr, s);
+    if (!st) st = ddf_alloc(&mdepth, count, s);
+    if (!st) st = ddf_alloc(&key, nr, s);
+    if (!st) st = ddf_alloc(&idx, nr, s);
+    if (!st && cudaMemsetAsync(mdepth, 0, sizeof(int32_t) * count, s) != cudaSuccess) st = DDF_ERR_CUDA;
+    if (!st) {
+        k_range_write<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, flag, off, rq);
+        ddf_count_launch();
+        const unsigned g = (unsigned)((nr + 255) / 256);
+        k_range_level<<<g, 256, 0, s>>>(nr, rq, p->seq, p->part_ptr, p->depth, moff, count, rmat, rlev, mdepth);
+        ddf_count_launch();
+        k_range_key<<<g, 256, 0, s>>>(nr, rmat, rlev, mdepth, key, idx);
+        ddf_count_launch();
+        if (cudaGetLastError() != cudaSuccess) st = DDF_ERR_CUDA;
+    }
+    if (!st) st = ddf_radix_sort_u32(key, idx, nr, 1u << ORDER_KEY_BITS, s);
+    if (!st) {
+        p->mrhs_q = rq;
+        p->mrhs_order = idx;
+        p->mrhs_nr = nr;
+        rq = idx = nullptr;
+    }
+    ddf_free(moff, s);
+    ddf_free(flag, s);
+    ddf_free(off, s);
+    ddf_free(rq, s);
+    ddf_free(rmat, s);
+    ddf_free(rlev, s);
+    ddf_free(mdepth, s);
+    ddf_free(key, s);
+    ddf_free(idx, s);
+    return st;
+}
+
 unsigned grid_units(int64_t nunits, int sm) {
     int64_t ctas = (nunits + DDF_WARPS_PER_CTA - 1) / DDF_WARPS_PER_CTA;
     int64_t cap = (int64_t)sm * 32;
@@ -861,9 +988,16 @@ SolveArgs<TV, TX> solve_args(const ddf_plan_s* p, const TV* val, const TX* dinv,
                              int32_t nrhs) {
     SolveArgs<TV, TX> A;
     A.n = p->n;
-    A.nunits = p->nunits[0];
     A.upt = p->mrhs_units_per_ticket > 0 ? p->mrhs_units_per_ticket : 1;
-    A.unit_q = p->unit_q;
+    if (p->mrhs_q) {   // a batch: ranges of one matrix each, in the order of build_mrhs_order
+        A.nunits = p->mrhs_nr;
+        A.order = p->mrhs_order;
+        A.unit_q = p->mrhs_q;
+    } else {
+        A.nunits = p->nunits[0];
+        A.order = nullptr;
+        A.unit_q = p->unit_q;
+    }
     A.seq = p->seq;
     A.st = p->starts;
     A.col = p->col;
@@ -1072,7 +1206,17 @@ ddf_status ddf_inspect_batch(const ddf_csr* mats, int32_t count, ddf_kind kind, 
         ddf_plan_destroy(p);
         return st;
     }
-    return ddf_finish_plan(p, rp, ci, v, s, out);
+    st = ddf_finish_plan(p, rp, ci, v, s, out);
+    if (st || kind != DDF_SPTRSV) return st;
+    std::vector<int32_t> moff((size_t)count);
+    for (int32_t i = 0, r = 0; i < count; r += mats[i].n_rows, ++i) moff[(size_t)i] = r;
+    st = build_mrhs_order(*out, moff, s);
+    if (!st && cudaStreamSynchronize(s) != cudaSuccess) st = DDF_ERR_CUDA;
+    if (st) {
+        ddf_plan_destroy(*out);
+        *out = nullptr;
+    }
+    return st;
 }
 
 ddf_status ddf_spmm(ddf_plan_t p, const void* X, void* Y, int32_t nrhs, ddf_dtype dtype, ddf_stream_t stream) {

@@ -57,6 +57,8 @@ void release(ddf_plan_s* p) {
     for (int k = 0; k < 3; ++k) ddf_free(p->units[k], s);
     for (int k = 0; k < 2; ++k) ddf_free(p->tiles[k], s);
     ddf_free(p->unit_q, s);
+    ddf_free(p->mrhs_order, s);
+    ddf_free(p->mrhs_q, s);
     ddf_free(p->long_q, s);
     ddf_free(p->status, s);
     ddf_free(p->ticket, s);
