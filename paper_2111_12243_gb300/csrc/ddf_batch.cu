@@ -660,6 +660,7 @@ __device__ __forceinline__ void grow_solve(const QRow<TX, LY::VEC>& m, const int
 }
 
 constexpr int SPTRSM_MIN_CTAS = 2;   // resident CTAs per SM the register budget is cut for
+constexpr int SEG_POINTS = 64;       // batch solve: rows of more points run as segments on several warps
 
 // Operands of the multi-RHS solve: its work ranges (the plan's units, or for
 // a batch the units split where the matrix changes: first positions, and the
@@ -671,8 +672,11 @@ struct SolveArgs {
     int32_t n;
     int64_t nunits;
     int32_t upt;
-    const int32_t* order;   // units in ticket order (NULL: level order)
+    const int32_t* order;   // items in ticket order (NULL: level order)
     const int32_t* unit_q;
+    const int2* seg;        // per item: (segment, first partial-sum slot), x = -1 for a range; NULL: no segments
+    TX* part;               // partial sums, NRHS_MAX per slot
+    uint32_t* cnt;          // segments finished, per long row
     const int32_t* seq;
     const int32_t* st;
     const int32_t* col;
@@ -685,6 +689,100 @@ struct SolveArgs {
     int32_t* status;
     int64_t cap_ns;
 };
+
+// Segment s of the long row at position q (points s SEG_POINTS .. s
+// SEG_POINTS + SEG_POINTS - 1) on one warp: its partial sums go to slot
+// g0 + s; the warp that finishes the row's last segment adds the slots in
+// segment order, solves the row and resets the row's counter for the next
+// solve.  Segments never wait on one another, so the ticket argument holds.
+template <typename TV, typename TX, class LY>
+__device__ __forceinline__ void solve_segment(const SolveArgs<TV, TX>& A, int64_t q, int32_t s, int32_t g0,
+                                              int lane) {
+    using V = typename LY::V;
+    using RBx = RB<TX>;
+    using U = typename V::U;
+    constexpr int VEC = LY::VEC, G = LY::G, NL = LY::NL, SUB = LY::SUB;
+    const int g = lane / LY::LP, c = lane % LY::LP;
+    const bool on = c * VEC < A.nrhs;
+    uint32_t* abort_flag = A.ticket + 1;
+    const int32_t kb = A.st[q], L = A.st[q + 1] - kb;
+    const int32_t S = (L + SEG_POINTS - 1) / SEG_POINTS;
+    const int32_t pb = s * SEG_POINTS, pe = min(L, pb + SEG_POINTS);
+    TX acc[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[v] = (TX)0;
+    for (int32_t p0 = pb; p0 < pe; p0 += 32) {
+        TX pv = (TX)0;
+        int32_t pj = 0;
+        if (p0 + lane < pe) {
+            pv = ddf_cvt<TX>(A.val[kb + p0 + lane]);
+            pj = A.col[kb + p0 + lane];
+        }
+        const int32_t cnt = min(32, pe - p0);
+        for (int32_t s0 = 0; s0 < cnt; s0 += SUB) {
+            U xb[NL][VEC];
+            TX av[NL];
+            int32_t jv[NL];
+#pragma unroll
+            for (int k = 0; k < NL; ++k) {
+                const int t = s0 + k * G + g;
+                av[k] = __shfl_sync(0xffffffffu, pv, t & 31);
+                jv[k] = __shfl_sync(0xffffffffu, pj, t & 31);
+                if (on && t < cnt) {
+                    V::ld_relaxed(A.X + (int64_t)jv[k] * A.nrhs + c * VEC, xb[k]);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) xb[k][v] = (U)0;
+                }
+            }
+            if (on) {
+                const int32_t mine = cnt > s0 + g ? (cnt - s0 - g + G - 1) / G : 0;
+                settle<V, TX, NL, VEC>(xb, jv, mine, A.X, A.nrhs, c, A.status, abort_flag, A.cap_ns);
+#pragma unroll
+                for (int k = 0; k < NL; ++k)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) acc[v] += av[k] * RBx::val(xb[k][v]);
+            }
+        }
+    }
+    group_sum<TX, LY::LP, VEC>(acc);
+    if (g == 0 && on) {
+        U bits[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) bits[v] = RBx::bits(acc[v]);
+        V::st_relaxed(A.part + (int64_t)(g0 + s) * NRHS_MAX + c * VEC, bits);
+    }
+    __syncwarp();
+    __threadfence();
+    uint32_t done = 0;
+    if (lane == 0) done = atomicAdd(A.cnt + g0, 1u);
+    done = __shfl_sync(0xffffffffu, done, 0);
+    if (done != (uint32_t)(S - 1)) return;
+    __threadfence();
+    if (g == 0 && on) {
+        TX tot[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) tot[v] = (TX)0;
+        for (int32_t k = 0; k < S; ++k) {
+            U pb2[VEC];
+            V::ld_relaxed(A.part + (int64_t)(g0 + k) * NRHS_MAX + c * VEC, pb2);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) tot[v] += RBx::val(pb2[v]);
+        }
+        const int32_t r = A.seq[q];
+        const TX di = A.dinv[q];
+        TX bv[VEC];
+        V::ld_nc(A.B + (int64_t)r * A.nrhs + c * VEC, bv);
+        U bits[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            bits[v] = RBx::bits((bv[v] - tot[v]) * di);
+            if (bits[v] == RBx::SENT) bits[v] = RBx::CANON;
+        }
+        V::st_relaxed(A.X + (int64_t)r * A.nrhs + c * VEC, bits);
+    }
+    if (lane == 0) A.cnt[g0] = 0u;
+}
 
 // Ranges at ticket positions u0 .. u1 - 1 of the solve on one warp, in order.
 // Inside a range (rows of one codelet, so of one level: they never read one
@@ -700,6 +798,13 @@ __device__ __forceinline__ void solve_units(const SolveArgs<TV, TX>& A, int64_t 
     uint32_t* abort_flag = A.ticket + 1;
     for (int64_t i = u0; i < u1; ++i) {
         const int64_t u = A.order ? (int64_t)A.order[i] : i;
+        if (A.seg) {
+            const int2 sg = A.seg[u];
+            if (sg.x >= 0) {
+                solve_segment<TV, TX, LY>(A, A.unit_q[u], sg.x, sg.y, lane);
+                continue;
+            }
+        }
         const int64_t qa = A.unit_q[u];
         const int64_t qz = (u + 1 < A.nunits) ? (int64_t)A.unit_q[u + 1] : (int64_t)A.n;
         if constexpr (LP == 32) {
@@ -804,17 +909,21 @@ k_batch(SolveArgs<TV, TX> S, MulArgs<TV, TX> M) {
     }
 }
 
-// Ticket order of a batch's solve.  In the block-diagonal plan, level l
-// holds the rows of every matrix at its own level l, so in plain level order
-// the deep matrices' last levels (few rows each, a chain of dependency hops)
-// run only after the shallow matrices' wide levels are done.  The solve's
-// work ranges are the plan's units split where the matrix changes (a codelet
-// may run across the end of one matrix's rows into the next one's); they
-// are sorted by normalized level, l / (depth of their matrix + 1), ties in
-// level order, which spreads every matrix over the whole run: the deep
-// chains advance beside the wide levels.  The order is topological: a
-// range's dependencies are rows of its own matrix at lower levels, whose
-// keys are no larger and which come first among equal keys.
+// Work items and ticket order of a batch's solve.  In the block-diagonal
+// plan, level l holds the rows of every matrix at its own level l, so in
+// plain level order the deep matrices' last levels (few rows each, a chain
+// of dependency hops) run only after the shallow matrices' wide levels are
+// done.  The solve's items are the plan's units split where the matrix
+// changes (a codelet may run across the end of one matrix's rows into the
+// next one's) and around rows of more than SEG_POINTS points; such a row
+// becomes ceil(L / SEG_POINTS) segment items that different warps run at the
+// same time (the last one to finish adds the partial sums in segment order).
+// The items are sorted by normalized level, l / (depth of their matrix + 1),
+// ties in level order, which spreads every matrix over the whole run: the
+// deep chains advance beside the wide levels.  The order is topological: an
+// item's dependencies are rows of its own matrix at lower levels, whose keys
+// are no larger and which come first among equal keys; segments of one row
+// never wait on one another.
 constexpr int ORDER_KEY_BITS = 20;
 
 __device__ __forceinline__ int32_t last_le(const int32_t* __restrict__ a, int32_t n, int32_t v) {
@@ -827,14 +936,21 @@ __device__ __forceinline__ int32_t last_le(const int32_t* __restrict__ a, int32_
     return lo;
 }
 
-// flag[q] = 1 where a range starts: a unit's first position, or a position
-// whose row belongs to another matrix than the row before it
+__device__ __forceinline__ bool long_row(const int32_t* __restrict__ st, int64_t q) {
+    return st[q + 1] - st[q] > SEG_POINTS;
+}
+
+// flag[q] = 1 where a range starts: a unit's first position, a position
+// whose row belongs to another matrix than the row before it, a long row,
+// or the position after a long row
 __global__ void k_range_flags(int32_t n, int64_t nu, const int32_t* __restrict__ unit_q,
-                              const int32_t* __restrict__ seq, const int32_t* __restrict__ moff, int32_t count,
-                              int32_t* __restrict__ flag) {
+                              const int32_t* __restrict__ seq, const int32_t* __restrict__ st,
+                              const int32_t* __restrict__ moff, int32_t count, int32_t* __restrict__ flag) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nu) flag[unit_q[i]] = 1;
-    if (i > 0 && i < n && last_le(moff, count, seq[i]) != last_le(moff, count, seq[i - 1])) flag[i] = 1;
+    if (i >= n) return;
+    if (long_row(st, i) || (i > 0 && long_row(st, i - 1))) flag[i] = 1;
+    if (i > 0 && last_le(moff, count, seq[i]) != last_le(moff, count, seq[i - 1])) flag[i] = 1;
 }
 
 __global__ void k_range_write(int32_t n, const int32_t* __restrict__ flag, const int64_t* __restrict__ off,
@@ -843,10 +959,13 @@ __global__ void k_range_write(int32_t n, const int32_t* __restrict__ flag, const
     if (q < n && flag[q]) rq[off[q]] = (int32_t)q;
 }
 
+// per range: its matrix and level (and the matrix's depth), its items (1, or
+// the segments of a long row) and partial-sum slots (0, or one per segment)
 __global__ void k_range_level(int64_t nr, const int32_t* __restrict__ rq, const int32_t* __restrict__ seq,
-                              const int32_t* __restrict__ part_ptr, int32_t depth, const int32_t* __restrict__ moff,
-                              int32_t count, int32_t* __restrict__ rmat, int32_t* __restrict__ rlev,
-                              int32_t* __restrict__ mdepth) {
+                              const int32_t* __restrict__ st, const int32_t* __restrict__ part_ptr, int32_t depth,
+                              const int32_t* __restrict__ moff, int32_t count, int32_t* __restrict__ rmat,
+                              int32_t* __restrict__ rlev, int32_t* __restrict__ mdepth, int32_t* __restrict__ nitem,
+                              int32_t* __restrict__ nslot) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nr) return;
     const int32_t q = rq[r];
@@ -855,28 +974,45 @@ __global__ void k_range_level(int64_t nr, const int32_t* __restrict__ rq, const 
     rmat[r] = m;
     rlev[r] = l;
     atomicMax(mdepth + m, l);
+    const int32_t L = st[q + 1] - st[q];
+    const int32_t S = L > SEG_POINTS ? (L + SEG_POINTS - 1) / SEG_POINTS : 0;   // a long row is a range of its own
+    nitem[r] = S > 0 ? S : 1;
+    nslot[r] = S;
 }
 
-__global__ void k_range_key(int64_t nr, const int32_t* __restrict__ rmat, const int32_t* __restrict__ rlev,
-                            const int32_t* __restrict__ mdepth, uint32_t* __restrict__ key, int32_t* __restrict__ idx) {
+__global__ void k_item_write(int64_t nr, const int32_t* __restrict__ rq, const int32_t* __restrict__ rmat,
+                             const int32_t* __restrict__ rlev, const int32_t* __restrict__ mdepth,
+                             const int32_t* __restrict__ nslot, const int64_t* __restrict__ ioff,
+                             const int64_t* __restrict__ soff, int32_t* __restrict__ iq, int2* __restrict__ iseg,
+                             uint32_t* __restrict__ key, int32_t* __restrict__ idx) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nr) return;
-    key[r] = (uint32_t)(((uint64_t)rlev[r] << ORDER_KEY_BITS) / ((uint64_t)mdepth[rmat[r]] + 1));
-    idx[r] = (int32_t)r;
+    const uint32_t k = (uint32_t)(((uint64_t)rlev[r] << ORDER_KEY_BITS) / ((uint64_t)mdepth[rmat[r]] + 1));
+    const int32_t S = nslot[r];
+    for (int32_t j = 0; j < (S > 0 ? S : 1); ++j) {
+        const int64_t i = ioff[r] + j;
+        iq[i] = rq[r];
+        iseg[i] = S > 0 ? make_int2(j, (int32_t)soff[r]) : make_int2(-1, 0);
+        key[i] = k;
+        idx[i] = (int32_t)i;
+    }
 }
 
-// Builds p->mrhs_q / mrhs_order / mrhs_nr for a batch solve plan whose
-// matrices start at rows moff_h[0 .. count - 1].
+// Builds the solve's items of a batch plan whose matrices start at rows
+// moff_h[0 .. count - 1].
 ddf_status build_mrhs_order(ddf_plan_s* p, const std::vector<int32_t>& moff_h, cudaStream_t s) {
     const int64_t nu = p->nunits[0];
     const int32_t n = p->n;
     const int32_t count = (int32_t)moff_h.size();
     if (nu < 1 || n < 2 || count < 2 || p->nblocks > 0) return DDF_OK;
-    int32_t *moff = nullptr, *flag = nullptr, *rq = nullptr, *rmat = nullptr, *rlev = nullptr, *mdepth = nullptr,
-            *idx = nullptr;
-    int64_t* off = nullptr;
+    int32_t *moff = nullptr, *flag = nullptr, *rq = nullptr, *rmat = nullptr, *rlev = nullptr, *mdepth = nullptr;
+    int32_t *nitem = nullptr, *nslot = nullptr, *iq = nullptr, *idx = nullptr;
+    int2* iseg = nullptr;
+    int64_t *off = nullptr, *ioff = nullptr, *soff = nullptr;
     uint32_t* key = nullptr;
-    int64_t nr = 0;
+    double* part = nullptr;
+    uint32_t* cnt = nullptr;
+    int64_t nr = 0, tot[2] = {0, 0};
     ddf_status st = ddf_alloc(&moff, count, s);
     if (!st) st = ddf_alloc(&flag, n, s);
     if (!st) st = ddf_alloc(&off, (int64_t)n + 1, s);
@@ -884,7 +1020,8 @@ ddf_status build_mrhs_order(ddf_plan_s* p, const std::vector<int32_t>& moff_h, c
         st = DDF_ERR_CUDA;
     if (!st && cudaMemsetAsync(flag, 0, sizeof(int32_t) * n, s) != cudaSuccess) st = DDF_ERR_CUDA;
     if (!st) {
-        k_range_flags<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, nu, p->unit_q, p->seq, moff, count, flag);
+        k_range_flags<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, nu, p->unit_q, p->seq, p->starts, moff, count,
+                                                                   flag);
         ddf_count_launch();
         if (cudaGetLastError() != cudaSuccess) st = DDF_ERR_CUDA;
     }
@@ -895,26 +1032,53 @@ ddf_status build_mrhs_order(ddf_plan_s* p, const std::vector<int32_t>& moff_h, c
     if (!st) st = ddf_alloc(&rq, nr, s);
     if (!st) st = ddf_alloc(&rmat, nr, s);
     if (!st) st = ddf_alloc(&rlev, nr, s);
+    if (!st) st = ddf_alloc(&nitem, nr, s);
+    if (!st) st = ddf_alloc(&nslot, nr, s);
+    if (!st) st = ddf_alloc(&ioff, nr + 1, s);
+    if (!st) st = ddf_alloc(&soff, nr + 1, s);
     if (!st) st = ddf_alloc(&mdepth, count, s);
-    if (!st) st = ddf_alloc(&key, nr, s);
-    if (!st) st = ddf_alloc(&idx, nr, s);
     if (!st && cudaMemsetAsync(mdepth, 0, sizeof(int32_t) * count, s) != cudaSuccess) st = DDF_ERR_CUDA;
     if (!st) {
+        const unsigned g = (unsigned)((nr + 255) / 256);
         k_range_write<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, flag, off, rq);
         ddf_count_launch();
-        const unsigned g = (unsigned)((nr + 255) / 256);
-        k_range_level<<<g, 256, 0, s>>>(nr, rq, p->seq, p->part_ptr, p->depth, moff, count, rmat, rlev, mdepth);
-        ddf_count_launch();
-        k_range_key<<<g, 256, 0, s>>>(nr, rmat, rlev, mdepth, key, idx);
+        k_range_level<<<g, 256, 0, s>>>(nr, rq, p->seq, p->starts, p->part_ptr, p->depth, moff, count, rmat, rlev,
+                                       mdepth, nitem, nslot);
         ddf_count_launch();
         if (cudaGetLastError() != cudaSuccess) st = DDF_ERR_CUDA;
     }
-    if (!st) st = ddf_radix_sort_u32(key, idx, nr, 1u << ORDER_KEY_BITS, s);
+    if (!st) st = ddf_scan_i32_to_i64(nitem, ioff, nr, s);
+    if (!st) st = ddf_scan_i32_to_i64(nslot, soff, nr, s);
+    if (!st && (cudaMemcpyAsync(tot, ioff + nr, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaMemcpyAsync(tot + 1, soff + nr, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess))
+        st = DDF_ERR_CUDA;
+    const int64_t ni = tot[0], ns = tot[1];
+    if (!st) st = ddf_alloc(&iq, ni, s);
+    if (!st) st = ddf_alloc(&iseg, ni, s);
+    if (!st) st = ddf_alloc(&key, ni, s);
+    if (!st) st = ddf_alloc(&idx, ni, s);
+    if (!st) st = ddf_alloc(&part, ns * NRHS_MAX, s);
+    if (!st) st = ddf_alloc(&cnt, ns, s);
+    if (!st && ns > 0 && cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * ns, s) != cudaSuccess) st = DDF_ERR_CUDA;
     if (!st) {
-        p->mrhs_q = rq;
+        k_item_write<<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(nr, rq, rmat, rlev, mdepth, nslot, ioff, soff, iq,
+                                                                   iseg, key, idx);
+        ddf_count_launch();
+        if (cudaGetLastError() != cudaSuccess) st = DDF_ERR_CUDA;
+    }
+    if (!st) st = ddf_radix_sort_u32(key, idx, ni, 1u << ORDER_KEY_BITS, s);
+    if (!st) {
+        p->mrhs_q = iq;
+        p->mrhs_seg = iseg;
         p->mrhs_order = idx;
-        p->mrhs_nr = nr;
-        rq = idx = nullptr;
+        p->mrhs_nr = ni;
+        p->mrhs_part = part;
+        p->mrhs_cnt = cnt;
+        iq = idx = nullptr;
+        iseg = nullptr;
+        part = nullptr;
+        cnt = nullptr;
     }
     ddf_free(moff, s);
     ddf_free(flag, s);
@@ -922,9 +1086,17 @@ ddf_status build_mrhs_order(ddf_plan_s* p, const std::vector<int32_t>& moff_h, c
     ddf_free(rq, s);
     ddf_free(rmat, s);
     ddf_free(rlev, s);
+    ddf_free(nitem, s);
+    ddf_free(nslot, s);
+    ddf_free(ioff, s);
+    ddf_free(soff, s);
     ddf_free(mdepth, s);
+    ddf_free(iq, s);
+    ddf_free(iseg, s);
     ddf_free(key, s);
     ddf_free(idx, s);
+    ddf_free(part, s);
+    ddf_free(cnt, s);
     return st;
 }
 
@@ -989,14 +1161,20 @@ SolveArgs<TV, TX> solve_args(const ddf_plan_s* p, const TV* val, const TX* dinv,
     SolveArgs<TV, TX> A;
     A.n = p->n;
     A.upt = p->mrhs_units_per_ticket > 0 ? p->mrhs_units_per_ticket : 1;
-    if (p->mrhs_q) {   // a batch: ranges of one matrix each, in the order of build_mrhs_order
+    if (p->mrhs_q) {   // a batch: the items and order of build_mrhs_order
         A.nunits = p->mrhs_nr;
         A.order = p->mrhs_order;
         A.unit_q = p->mrhs_q;
+        A.seg = p->mrhs_seg;
+        A.part = reinterpret_cast<TX*>(p->mrhs_part);
+        A.cnt = p->mrhs_cnt;
     } else {
         A.nunits = p->nunits[0];
         A.order = nullptr;
         A.unit_q = p->unit_q;
+        A.seg = nullptr;
+        A.part = nullptr;
+        A.cnt = nullptr;
     }
     A.seq = p->seq;
     A.st = p->starts;

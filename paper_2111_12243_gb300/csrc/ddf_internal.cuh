@@ -106,10 +106,15 @@ struct ddf_plan_s {
                                   // units[0] = all, level order
     int64_t nunits[3];
     int32_t* unit_q;              // SpTRSV: first position of each unit of units[0]
-    int32_t* mrhs_q;              // SpTRSV batch plans: first positions of the multi-RHS solve's ranges
-                                  // (units[0] split where the matrix changes; NULL: the units themselves)
-    int32_t* mrhs_order;          // ... and those ranges in the solve's ticket order
-    int64_t mrhs_nr;
+    // SpTRSV batch plans, the multi-RHS solve's work items (NULL: the units
+    // themselves): ranges of positions (units[0] split where the matrix
+    // changes) and segments of long rows
+    int32_t* mrhs_q;              // first position of each item
+    int2* mrhs_seg;               // (segment of its row, first partial-sum slot of the row); x = -1: a range
+    int32_t* mrhs_order;          // the items in the solve's ticket order
+    int64_t mrhs_nr;              // items
+    double* mrhs_part;            // partial sums of the segments: 32 slots of 8 bytes per segment
+    uint32_t* mrhs_cnt;           // segments finished, per long row (at its first slot)
     int32_t* long_q;              // SpMV: positions of the PSC II rows of more than DDF_LONG_ROW
                                   // points (each a one-row unit of units[2], run one CTA per row)
     int64_t nlong;

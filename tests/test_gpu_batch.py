@@ -297,3 +297,50 @@ def test_batch_run_argument_errors(small_batch):
     assert e.value.status == 1
     ddf.ddf_batch_run(p, X, Y, q, B, Xs, 4)
     assert ddf.ddf_get_status(q) == 0
+
+
+def long_row_lower(n=2500, seed=21):
+    """A diagonally dominant lower triangle whose every 17th row reads the
+    previous 70 .. 1100 rows (rows longer than a solve segment), the rest a
+    band of 3."""
+    rng = np.random.default_rng(seed)
+    rows = []
+    for i in range(n):
+        if i % 17 == 0 and i > 70:
+            k = int(min(i, rng.integers(70, 1100)))
+            cols = np.sort(rng.choice(i, k, replace=False))
+        else:
+            cols = np.arange(max(0, i - 3), i)
+        rows.append(np.concatenate([cols, [i]]).astype(np.int32))
+    rp = np.zeros(n + 1, np.int64)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    ci = np.concatenate(rows)
+    v = rng.standard_normal(ci.size) * 0.01
+    v[rp[1:] - 1] = 1.0 + np.abs(rng.standard_normal(n))
+    return synth.CSR(n, n, rp.astype(np.int32), ci, v)
+
+
+@pytest.mark.parametrize("nrhs,dt", [(32, torch.float32), (5, torch.float64), (16, torch.float64)])
+def test_sptrsm_long_rows_in_segments(small_batch, nrhs, dt):
+    # a batch whose rows of more than 64 points are solved in segments on
+    # several warps, their partial sums added in a fixed order: results
+    # within the oracle's tolerance and the same on every call
+    lows = [long_row_lower(), synth.lower_triangle(small_batch[2]), long_row_lower(1800, 22)]
+    lo = block_diag(lows)
+    opts = {"store_dtype": ddf.DDF_F32} if dt == torch.float32 else {}
+    q = batch_plan(lows, ddf.DDF_SPTRSV, **opts)
+    B = np.random.default_rng(nrhs).uniform(-1, 1, (lo.n_rows, nrhs))
+    Bd = torch.from_numpy(B).to(dt).cuda()
+    Xs = torch.empty((lo.n_rows, nrhs), dtype=dt, device="cuda")
+    ddf.ddf_sptrsm(q, Bd, Xs, nrhs)
+    x0 = Xs.clone()
+    for _ in range(2):
+        ddf.ddf_sptrsm(q, Bd, Xs, nrhs)
+        assert torch.equal(Xs, x0)
+    assert ddf.ddf_get_status(q) == 0
+    Xh = Xs.double().cpu().numpy()
+    for k in range(nrhs):
+        bk = Bd[:, k].double().cpu().numpy()
+        rx = oracle.sptrsv(lo, bk)
+        tol = 1e-5 if dt == torch.float32 else TOL
+        assert np.linalg.norm(Xh[:, k] - rx) <= tol * np.linalg.norm(rx)
