@@ -678,6 +678,7 @@ def run_batch(args, ddf, torch, dev, stream, flush, nrhs=32, reps=5):
             "tile_sptrsm_units_per_ticket": tile_trsv, "graph_ms": round(t_graph, 4), "graph_status": st_graph,
             "graph_gbs": round((bytes_spmm + bytes_trsm) / (t_graph * 1e-3) / 1e9, 1),
             "graph_launches": launches_one, "graph_two_calls_ms": round(t_graph2, 4),
+            "graph_two_calls_gbs": round((bytes_spmm + bytes_trsm) / (t_graph2 * 1e-3) / 1e9, 1),
             "graph_two_calls_launches": launches_two,
             "spmm_ms": round(t_spmm, 4), "spmm_gbs": round(bytes_spmm / (t_spmm * 1e-3) / 1e9, 1),
             "sptrsm_ms": round(t_trsm, 4), "sptrsm_gbs": round(bytes_trsm / (t_trsm * 1e-3) / 1e9, 1),

@@ -396,8 +396,12 @@ __device__ __forceinline__ void spmm_tile(const MulArgs<TV, TX>& A, const dtile&
 }
 
 // Work unit array k (k < 3) or tile array k - 3 of the plan, one warp per item.
+// The products are bound by L2 latency: four resident CTAs per SM (64
+// registers a thread, a few spilled) measured faster than three.
+constexpr int SPMM_MIN_CTAS = 4;
+
 template <typename TV, typename TX, class LY>
-__global__ void __launch_bounds__(DDF_CTA_THREADS) k_spmm(MulArgs<TV, TX> A, int k) {
+__global__ void __launch_bounds__(DDF_CTA_THREADS, SPMM_MIN_CTAS) k_spmm(MulArgs<TV, TX> A, int k) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t count = k < 3 ? A.nunits[k] : A.ntiles[k - 3];
