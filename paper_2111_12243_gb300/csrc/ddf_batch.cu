@@ -1002,12 +1002,13 @@ __global__ void k_item_write(int64_t nr, const int32_t* __restrict__ rq, const i
     }
 }
 
+}  // namespace
+
 // Builds the solve's items of a batch plan whose matrices start at rows
-// moff_h[0 .. count - 1].
-ddf_status build_mrhs_order(ddf_plan_s* p, const std::vector<int32_t>& moff_h, cudaStream_t s) {
+// moff_h[0 .. count - 1] (host array) and keeps those offsets in the plan.
+ddf_status ddf_build_mrhs_items(ddf_plan_s* p, const int32_t* moff_h, int32_t count, cudaStream_t s) {
     const int64_t nu = p->nunits[0];
     const int32_t n = p->n;
-    const int32_t count = (int32_t)moff_h.size();
     if (nu < 1 || n < 2 || count < 2 || p->nblocks > 0) return DDF_OK;
     int32_t *moff = nullptr, *flag = nullptr, *rq = nullptr, *rmat = nullptr, *rlev = nullptr, *mdepth = nullptr;
     int32_t *nitem = nullptr, *nslot = nullptr, *iq = nullptr, *idx = nullptr;
@@ -1020,7 +1021,7 @@ ddf_status build_mrhs_order(ddf_plan_s* p, const std::vector<int32_t>& moff_h, c
     ddf_status st = ddf_alloc(&moff, count, s);
     if (!st) st = ddf_alloc(&flag, n, s);
     if (!st) st = ddf_alloc(&off, (int64_t)n + 1, s);
-    if (!st && cudaMemcpyAsync(moff, moff_h.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    if (!st && cudaMemcpyAsync(moff, moff_h, sizeof(int32_t) * count, cudaMemcpyHostToDevice, s) != cudaSuccess)
         st = DDF_ERR_CUDA;
     if (!st && cudaMemsetAsync(flag, 0, sizeof(int32_t) * n, s) != cudaSuccess) st = DDF_ERR_CUDA;
     if (!st) {
@@ -1079,10 +1080,14 @@ ddf_status build_mrhs_order(ddf_plan_s* p, const std::vector<int32_t>& moff_h, c
         p->mrhs_nr = ni;
         p->mrhs_part = part;
         p->mrhs_cnt = cnt;
+        p->mrhs_ns = ns;
+        p->mrhs_moff = moff;
+        p->mrhs_nmat = count;
         iq = idx = nullptr;
         iseg = nullptr;
         part = nullptr;
         cnt = nullptr;
+        moff = nullptr;
     }
     ddf_free(moff, s);
     ddf_free(flag, s);
@@ -1103,6 +1108,8 @@ ddf_status build_mrhs_order(ddf_plan_s* p, const std::vector<int32_t>& moff_h, c
     ddf_free(cnt, s);
     return st;
 }
+
+namespace {
 
 unsigned grid_units(int64_t nunits, int sm) {
     int64_t ctas = (nunits + DDF_WARPS_PER_CTA - 1) / DDF_WARPS_PER_CTA;
@@ -1392,7 +1399,7 @@ ddf_status ddf_inspect_batch(const ddf_csr* mats, int32_t count, ddf_kind kind, 
     if (st || kind != DDF_SPTRSV) return st;
     std::vector<int32_t> moff((size_t)count);
     for (int32_t i = 0, r = 0; i < count; r += mats[i].n_rows, ++i) moff[(size_t)i] = r;
-    st = build_mrhs_order(*out, moff, s);
+    st = ddf_build_mrhs_items(*out, moff.data(), count, s);
     if (!st && cudaStreamSynchronize(s) != cudaSuccess) st = DDF_ERR_CUDA;
     if (st) {
         ddf_plan_destroy(*out);

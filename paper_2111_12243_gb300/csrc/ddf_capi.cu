@@ -62,6 +62,7 @@ void release(ddf_plan_s* p) {
     ddf_free(p->mrhs_seg, s);
     ddf_free(p->mrhs_part, s);
     ddf_free(p->mrhs_cnt, s);
+    ddf_free(p->mrhs_moff, s);
     ddf_free(p->long_q, s);
     ddf_free(p->status, s);
     ddf_free(p->ticket, s);

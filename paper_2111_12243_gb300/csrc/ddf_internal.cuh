@@ -115,6 +115,9 @@ struct ddf_plan_s {
     int64_t mrhs_nr;              // items
     double* mrhs_part;            // partial sums of the segments: 32 slots of 8 bytes per segment
     uint32_t* mrhs_cnt;           // segments finished, per long row (at its first slot)
+    int64_t mrhs_ns;              // partial-sum slots
+    int32_t* mrhs_moff;           // first row of each matrix of the batch (saved with the plan)
+    int32_t mrhs_nmat;
     int32_t* long_q;              // SpMV: positions of the PSC II rows of more than DDF_LONG_ROW
                                   // points (each a one-row unit of units[2], run one CTA per row)
     int64_t nlong;
@@ -229,6 +232,8 @@ ddf_status ddf_compute_stats(ddf_plan_s* p);
 ddf_status ddf_build_units(ddf_plan_s* p, cudaStream_t s);
 ddf_status ddf_mark_tiles(ddf_plan_s* p, cudaStream_t s);
 ddf_status ddf_build_unit_q(ddf_plan_s* p, cudaStream_t s);
+// ddf_batch.cu: the multi-RHS solve's work items of a batch plan whose matrices start at rows moff[0 .. count - 1]
+ddf_status ddf_build_mrhs_items(ddf_plan_s* p, const int32_t* moff, int32_t count, cudaStream_t s);
 ddf_status ddf_build_long_rows(ddf_plan_s* p, cudaStream_t s);
 // ddf_capi.cu
 ddf_status ddf_new_plan(ddf_kind kind, const ddf_opts* o, cudaStream_t s, int32_t n, int32_t n_cols, int64_t nnz,

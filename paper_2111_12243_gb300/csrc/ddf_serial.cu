@@ -17,12 +17,12 @@
 namespace {
 
 constexpr char MAGIC[8] = {'D', 'D', 'F', 'P', 'L', 'A', 'N', '1'};
-constexpr int32_t VERSION = 5;
+constexpr int32_t VERSION = 6;
 
 struct Header {
     char magic[8];
     int32_t version, kind, n, n_cols, depth, has_values, vdtype, mrhs_units_per_ticket;
-    int32_t nlevels, nblocks;
+    int32_t nlevels, nblocks, mrhs_nmat;
     int64_t nnz, npts, ncod, ncod_type[3], nunits[3], nchunks;
     int64_t ntiles[2];
     ddf_opts opts;
@@ -79,6 +79,8 @@ std::vector<Piece> pieces(ddf_plan_s* p, const Header& h, void** slots[24]) {
             add((void**)&p->chunk_meta, 4 * (size_t)h.nchunks);
             add((void**)&p->blk_chunk, 4 * (size_t)(h.nblocks + 1));
         }
+        // a batch plan: its matrices' first rows, from which the load rebuilds the multi-RHS solve's items
+        if (h.mrhs_nmat > 0) add((void**)&p->mrhs_moff, 4 * (size_t)h.mrhs_nmat);
     }
     if (lp) {
         add((void**)&p->val_lp, value_size(h.vdtype) * (size_t)nv);
@@ -104,6 +106,7 @@ Header header_of(ddf_plan_s* p) {
     h.mrhs_units_per_ticket = p->mrhs_units_per_ticket;
     h.nlevels = p->nlevels;
     h.nblocks = p->nblocks;
+    h.mrhs_nmat = p->mrhs_nmat;
     h.nchunks = p->nchunks;
     h.nnz = p->nnz;
     h.npts = p->npts;
@@ -174,6 +177,8 @@ ddf_status ddf_plan_load(const void* buf, size_t len, ddf_stream_t stream, ddf_p
     // the sizes below (no overflow) before they are summed
     const int64_t cap = (int64_t)len;
     if (h.nblocks < 0 || h.nlevels < 0 || h.nchunks < 0 || h.nchunks > (int64_t)len || (h.nblocks > 0 && (h.kind != DDF_SPTRSV || h.opts.coarsen_rows < 1)))
+        return DDF_ERR_ARG;
+    if (h.mrhs_nmat < 0 || (h.mrhs_nmat > 0 && (h.kind != DDF_SPTRSV || h.mrhs_nmat > h.n || h.nblocks > 0)))
         return DDF_ERR_ARG;
     if (h.n >= cap || h.depth >= cap || h.nblocks >= cap || h.nnz > cap || h.npts > cap || h.ncod > cap || h.nunits[0] > cap ||
         h.nunits[1] > cap || h.nunits[2] > cap || h.ntiles[0] < 0 || h.ntiles[1] < 0 || h.ntiles[0] > cap ||
@@ -246,6 +251,21 @@ ddf_status ddf_plan_load(const void* buf, size_t len, ddf_stream_t stream, ddf_p
     // derived from the validated units: the solve's unit positions, the
     // SpMV's long PSC II rows
     if (!st && h.kind == DDF_SPTRSV) st = ddf_build_unit_q(p, s);
+    // a batch plan's multi-RHS solve items, rebuilt from the matrices' first
+    // rows once those are checked (0 first, non-decreasing, within n)
+    if (!st && h.mrhs_nmat > 0) {
+        std::vector<int32_t> moff((size_t)h.mrhs_nmat);
+        int32_t* dmoff = p->mrhs_moff;
+        p->mrhs_moff = nullptr;
+        p->mrhs_nmat = 0;
+        if (cudaMemcpyAsync(moff.data(), dmoff, 4 * moff.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            st = DDF_ERR_CUDA;
+        ddf_free(dmoff, s);
+        for (size_t i = 0; !st && i < moff.size(); ++i)
+            if ((i == 0 && moff[0] != 0) || (i > 0 && moff[i] < moff[i - 1]) || moff[i] > h.n) st = DDF_ERR_ARG;
+        if (!st) st = ddf_build_mrhs_items(p, moff.data(), h.mrhs_nmat, s);
+    }
     if (!st && h.kind == DDF_SPMV) st = ddf_build_long_rows(p, s);
     if (!st && cudaStreamSynchronize(s) != cudaSuccess) st = DDF_ERR_CUDA;
     if (st) {
