@@ -498,29 +498,61 @@ __global__ void k_rel_lens(int32_t n, const int32_t* __restrict__ perm, const in
     lens[q] = re[r] - rp[r] - 1;
 }
 
-__global__ void k_rel_gather(int32_t n, const int32_t* __restrict__ perm, const int32_t* __restrict__ rp,
-                             const int32_t* __restrict__ re, const int32_t* __restrict__ ci,
-                             const double* __restrict__ vals,
-                             const int32_t* __restrict__ st, int32_t* __restrict__ col,
-                             double* __restrict__ val, double* __restrict__ dinv, double* __restrict__ diag,
-                             int lanes) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lg = __ffs(lanes) - 1, li = (int)(t & (lanes - 1));
-    const int64_t q = t >> lg;
-    if (q >= n) return;
-    const int32_t r = perm[q];
-    const int32_t a = rp[r], e = re[r] - 1, d = st[q];
-    if (col) {
-#pragma unroll 4
-        for (int32_t k = a + li; k < e; k += lanes) col[d + (k - a)] = ci[k];
-    }
-    if (vals) {
-#pragma unroll 4
-        for (int32_t k = a + li; k < e; k += lanes) val[d + (k - a)] = vals[k];
-        if (li == 0) {
-            dinv[q] = 1.0 / vals[e];
-            if (diag) diag[q] = vals[e];
+// Copies the off-diagonal columns (col != NULL) and values (vals != NULL) of
+// the rows in level order, and 1 / L_qq (and L_qq when diag != NULL).  A warp
+// takes 32 consecutive positions, whose outputs are one contiguous stretch
+// st[q0] .. st[q0 + 32]: lane l finds the source of output element o = l, l +
+// 32, ... by a binary search over the positions' output starts (staged in
+// shared memory), so the writes are coalesced and the reads of a row's
+// points are contiguous across lanes.
+constexpr int REL_THREADS = 256;
+
+__global__ void __launch_bounds__(REL_THREADS)
+k_rel_gather(int32_t n, const int32_t* __restrict__ perm, const int32_t* __restrict__ rp,
+             const int32_t* __restrict__ re, const int32_t* __restrict__ ci, const double* __restrict__ vals,
+             const int32_t* __restrict__ st, int32_t* __restrict__ col, double* __restrict__ val,
+             double* __restrict__ dinv, double* __restrict__ diag) {
+    __shared__ int32_t sd_all[REL_THREADS / 32][32];
+    __shared__ int32_t sa_all[REL_THREADS / 32][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t* sd = sd_all[w];
+    int32_t* sa = sa_all[w];
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t gq = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gq * 32 < n; gq += nw) {
+        const int64_t q0 = gq * 32;
+        const int32_t R = (int32_t)min((int64_t)32, (int64_t)n - q0);
+        const int64_t q = q0 + lane;
+        int32_t a = 0, d = 0;
+        if (lane < R) {
+            const int32_t r = perm[q];
+            a = rp[r];
+            const int32_t e = re[r] - 1;   // the diagonal is last
+            d = st[q];
+            if (vals) {
+                const double dv = vals[e];
+                dinv[q] = 1.0 / dv;
+                if (diag) diag[q] = dv;
+            }
         }
+        const int32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+        const int32_t dend = st[q0 + R];
+        sd[lane] = d - d0;
+        sa[lane] = a;
+        __syncwarp();
+        const int32_t T = dend - d0;
+#pragma unroll 4
+        for (int32_t o = lane; o < T; o += 32) {
+            int32_t lo = 0, hi = R - 1;   // the last position whose output starts at or before o
+            while (lo < hi) {
+                const int32_t mid = (lo + hi + 1) >> 1;
+                if (sd[mid] <= o) lo = mid;
+                else hi = mid - 1;
+            }
+            const int32_t src = sa[lo] + (o - sd[lo]);
+            if (col) col[d0 + o] = ci[src];
+            if (vals) val[d0 + o] = vals[src];
+        }
+        __syncwarp();
     }
 }
 
@@ -1293,11 +1325,6 @@ int lanes_for_mean(int64_t entries, int64_t rows, int cap = 32) {
     return v;
 }
 
-// The level-order relayout reads a row only after two dependent loads (its
-// position's row, then the row's extent): at most 8 lanes per row, so that a
-// warp has several rows' chains in flight (elasticity 64^3: inspect(L)
-// 2.37-2.46 -> 2.21 ms against 32 lanes per row).
-constexpr int REL_GATHER_MAX_LANES = 8;
 
 // CSR validation: at most 4 lanes per row (inspect(L) of elasticity 64^3:
 // 2.22 ms with 32 lanes per row, 2.10 ms with 4, 2.14 ms with one)
@@ -1460,10 +1487,9 @@ ddf_status ddf_build_plan(ddf_plan_s* p, const int32_t* rowptr, const int32_t* c
         TRY(ddf_alloc(&p->dinv, n, s));
         if (p->opts.store_dtype != DDF_F64) TRY(ddf_alloc(&p->diag, n, s));
         if (n > 0) {
-            const int gv = lanes_for_mean(npts, n, REL_GATHER_MAX_LANES);
-            k_rel_gather<<<ddf_grid((int64_t)n * gv, TPB), TPB, 0, s>>>(n, p->seq, rowptr, rowend, colidx, values,
-                                                                        p->starts, p->col, p->val, p->dinv, p->diag,
-                                                                        gv);
+            const unsigned cap = (unsigned)(p->sm_count > 0 ? p->sm_count : 152) * 8;
+            k_rel_gather<<<ddf_grid(((int64_t)n + 31) / 32 * 32, REL_THREADS, cap), REL_THREADS, 0, s>>>(
+                n, p->seq, rowptr, rowend, colidx, values, p->starts, p->col, p->val, p->dinv, p->diag);
             ddf_count_launch();
         }
         DDF_CUDA_TRY(cudaGetLastError());
@@ -1815,11 +1841,10 @@ ddf_status ddf_gather_values(ddf_plan_s* p, const double* values, cudaStream_t s
     }
     int32_t n = p->n;
     if (n > 0) {
-        const int gv = lanes_for_mean(p->npts, n, REL_GATHER_MAX_LANES);
         const int32_t* re = p->orig_rowend ? p->orig_rowend : p->orig_rowptr + 1;
-        k_rel_gather<<<ddf_grid((int64_t)n * gv, TPB), TPB, 0, s>>>(n, p->seq, p->orig_rowptr, re, nullptr, values,
-                                                                   p->starts, nullptr, p->val, p->dinv, p->diag,
-                                                                   gv);
+        const unsigned cap = (unsigned)(p->sm_count > 0 ? p->sm_count : 152) * 8;
+        k_rel_gather<<<ddf_grid(((int64_t)n + 31) / 32 * 32, REL_THREADS, cap), REL_THREADS, 0, s>>>(
+            n, p->seq, p->orig_rowptr, re, nullptr, values, p->starts, nullptr, p->val, p->dinv, p->diag);
         ddf_count_launch();
     }
     DDF_CUDA_TRY(cudaGetLastError());
