@@ -15,7 +15,8 @@ step, inspection included.  Extra keys report:
   extra            other workloads (default the power-law matrix), each phase alone
   mixed_precision  FP32 / BF16 SpMV and refined SpTRSV on the 27-point stencil, integer
                    and N(0,1) values, errors against the CPU oracle
-  ablation_e5      plans restricted to BLAS + PSC II codelets against all types (Sec. V)
+  ablation_e5      plans restricted to BLAS + PSC II codelets against all types (Sec. V); Eq. 1's
+                   weights recalibrated on the GPU (ddf_tune_cost)
   blas_banded      a band matrix, whose plan is BLAS codelets
   batched          256 uneven matrices x 32 right-hand sides in one CUDA graph
 
@@ -769,19 +770,30 @@ def run_mixed(args, host, ddf, torch, dev, timed):
 def run_ablation(args, host, ddf, torch, dev, timed):
     """E5 (Sec. V, the BLAS-only comparison): plans restricted to BLAS codelets
     (plus PSC II, which covers whatever BLAS does not) against plans with every
-    codelet type, executors timed alone."""
+    codelet type, executors timed alone.  Also E2's GPU recalibration of Eq. 1
+    (ddf_tune_cost): the weight set it picks for each kernel, and the
+    executors on plans mined with those weights."""
     out = {}
+    td = lambda v: torch.from_numpy(np.ascontiguousarray(v)).to(dev)  # noqa: E731
     for nm in names(args.ablation):
         a, lo, x, b = host[nm] if nm in host else synth.workload(nm, args.scale)
         full = solo(ddf, torch, dev, timed, a, lo, x, b)
         ob = ddf.ddf_opts_default(allowed_types=ddf.DDF_ALLOW_BLAS | ddf.DDF_ALLOW_PSC2)
         bl = solo(ddf, torch, dev, timed, a, lo, x, b, ob, ob)
+        oa, ka = ddf.ddf_tune_cost(td(a.rowptr), td(a.colidx), td(a.values), a.n_cols, ddf.DDF_SPMV)
+        ol, kl = ddf.ddf_tune_cost(td(lo.rowptr), td(lo.colidx), td(lo.values), lo.n_cols, ddf.DDF_SPTRSV)
+        tu = solo(ddf, torch, dev, timed, a, lo, x, b, oa, ol) if (ka or kl) else full
         out[nm] = {"all_types": {k: full[k] for k in ("spmv_ms", "spmv_gbs", "sptrsv_ms", "sptrsv_gbs",
                                                      "codelets_spmv", "ops_spmv", "codelets_sptrsv")},
                    "blas_psc2": {k: bl[k] for k in ("spmv_ms", "spmv_gbs", "sptrsv_ms", "sptrsv_gbs",
                                                    "codelets_spmv", "ops_spmv", "codelets_sptrsv")},
                    "spmv_speedup_all_vs_blas": round(bl["spmv_ms"] / full["spmv_ms"], 3),
-                   "sptrsv_speedup_all_vs_blas": round(bl["sptrsv_ms"] / full["sptrsv_ms"], 3)}
+                   "sptrsv_speedup_all_vs_blas": round(bl["sptrsv_ms"] / full["sptrsv_ms"], 3),
+                   "eq1_tuned": {"spmv_weights": [oa.w_op, oa.w_codelet, oa.w_index],
+                                 "sptrsv_weights": [ol.w_op, ol.w_codelet, ol.w_index],
+                                 "spmv_ms": tu["spmv_ms"], "sptrsv_ms": tu["sptrsv_ms"],
+                                 "spmv_speedup_vs_default": round(full["spmv_ms"] / tu["spmv_ms"], 3),
+                                 "sptrsv_speedup_vs_default": round(full["sptrsv_ms"] / tu["sptrsv_ms"], 3)}}
     return out
 
 

@@ -292,6 +292,22 @@ DDF_API ddf_status ddf_batch_run(ddf_plan_t pa, const void* X, void* Y, ddf_plan
 DDF_API ddf_status ddf_tune(ddf_plan_t p, const void* in, void* out, int32_t nrhs, ddf_dtype dtype,
                             ddf_stream_t s, int32_t* best_unit_nnz);
 
+/*
+ * GPU recalibration of the cost model (Eq. 1, Sec. III-C).  The paper fits the
+ * model's weights to CPU timings (Fig. 5); here the weights are chosen on the
+ * GPU: the matrix A (with values) is inspected for `kind` with each of six
+ * weight sets (w_op, w_codelet, w_index) = (8, 32, 4) (the default byte
+ * costs), (8, 8, 4), (8, 128, 4), (8, 32, 1), (8, 32, 16) and (1, 3, 1) (the
+ * paper's CPU form), the executor is timed on each plan (CUDA events, the
+ * fastest of three runs after a warm-up, a vector of ones as input), and the
+ * fastest set is written into *o (its other fields are kept and used for
+ * every inspection).  *pick (may be NULL) receives the index of the chosen
+ * set.  DDF_ERR_ARG without values or for another kind; inspection and
+ * executor errors are returned as they are.  Allocates and frees its own
+ * vectors; synchronises s.
+ */
+DDF_API ddf_status ddf_tune_cost(const ddf_csr* A, ddf_kind kind, ddf_opts* o, ddf_stream_t s, int32_t* pick);
+
 /* Synchronise s, then return and clear the plan's device status word: the
  * errors only the executor can see while it runs the partitions of Sec. IV-A
  * in order (DDF_ERR_TIMEOUT: a dependency wait ran out).  DDF_OK when none

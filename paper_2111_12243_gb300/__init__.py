@@ -35,7 +35,7 @@ EXPORTS = ("ddf_opts_default", "ddf_inspect", "ddf_update_values", "ddf_spmv", "
            "ddf_get_status", "ddf_plan_stats", "ddf_plan_export", "ddf_plan_destroy",
            "ddf_status_string", "ddf_last_launches", "ddf_kernel_launches",
            "ddf_debug_set_dependency", "ddf_sptrsv_csr_noalloc", "ddf_spmv_lowp", "ddf_sptrsv_refine",
-           "ddf_inspect_batch", "ddf_spmm", "ddf_sptrsm", "ddf_batch_run", "ddf_tune", "ddf_plan_save",
+           "ddf_inspect_batch", "ddf_spmm", "ddf_sptrsm", "ddf_batch_run", "ddf_tune", "ddf_tune_cost", "ddf_plan_save",
            "ddf_plan_load", "ddf_plan_validate", "ddf_debug_fail_alloc")
 #: rows accepted by ddf_sptrsv_csr_noalloc (the size of its static scratch)
 DDF_NOALLOC_MAX_ROWS = 1 << 20
@@ -121,6 +121,8 @@ def lib():
         L.ddf_sptrsm.restype = ctypes.c_int
         L.ddf_batch_run.argtypes = [P, P, P, P, P, P, I32, ctypes.c_int, P]
         L.ddf_batch_run.restype = ctypes.c_int
+        L.ddf_tune_cost.argtypes = [P, ctypes.c_int, P, P, ctypes.POINTER(I32)]
+        L.ddf_tune_cost.restype = ctypes.c_int
         L.ddf_tune.argtypes = [P, P, P, I32, ctypes.c_int, P, ctypes.POINTER(I32)]
         L.ddf_tune.restype = ctypes.c_int
         L.ddf_plan_save.argtypes = [P, P, ctypes.POINTER(ctypes.c_size_t)]
@@ -221,7 +223,6 @@ def ddf_inspect(rowptr, colidx, values, n_cols: int, kind: int, opts: ddf_opts |
     h = ctypes.c_void_p()
     st = lib().ddf_inspect(ctypes.byref(A), int(kind), ctypes.byref(opts) if opts is not None else None,
                            _stream(stream), ctypes.byref(h))
-    del k1, k2, k3
     _check(st, "ddf_inspect")
     return Plan(h, int(kind), n_rows, int(n_cols))
 
@@ -348,6 +349,27 @@ def ddf_tune(plan: Plan, inp, out, nrhs: int, stream=None) -> int:
     best = ctypes.c_int32(0)
     _check(lib().ddf_tune(plan.handle, pi, po, int(nrhs), di, _stream(stream), ctypes.byref(best)), "ddf_tune")
     return int(best.value)
+
+
+def ddf_tune_cost(rowptr, colidx, values, n_cols: int, kind: int, opts: ddf_opts | None = None,
+                  stream=None):
+    """Pick Eq. 1's weights on the GPU by timing the executor of plans mined with
+    candidate weight sets; returns (options with the chosen weights, its index)."""
+    rp, dev_r, k1 = _ptr(rowptr, np.int32)
+    ci, dev_c, k2 = _ptr(colidx, np.int32)
+    va, dev_v, k3 = _ptr(values, np.float64)
+    if values is None or len({dev_r, dev_c, dev_v}) != 1:
+        raise ValueError("rowptr, colidx and values must be given, all on the device or all on the host")
+    A = ddf_csr(int(len(rowptr)) - 1, int(n_cols), int(len(colidx)), rp, ci, va, dev_r, 0)
+    o = ddf_opts()
+    if opts is not None:
+        ctypes.memmove(ctypes.byref(o), ctypes.byref(opts), ctypes.sizeof(o))
+    else:
+        lib().ddf_opts_default(ctypes.byref(o))
+    pick = ctypes.c_int32(-1)
+    _check(lib().ddf_tune_cost(ctypes.byref(A), int(kind), ctypes.byref(o), _stream(stream), ctypes.byref(pick)),
+           "ddf_tune_cost")
+    return o, int(pick.value)
 
 
 def ddf_plan_save(plan: Plan) -> bytes:

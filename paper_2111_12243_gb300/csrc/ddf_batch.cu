@@ -1304,6 +1304,11 @@ ddf_status run_multi(ddf_plan_s* p, const void* in, void* out, int32_t nrhs, ddf
                                        s);
 }
 
+__global__ void k_fill_f64(double* __restrict__ a, int64_t n, double v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+
 bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
     return na > 0 && nb > 0 && (const char*)a < (const char*)b + nb && (const char*)b < (const char*)a + na;
 }
@@ -1506,6 +1511,64 @@ ddf_status ddf_tune(ddf_plan_t p, const void* in, void* out, int32_t nrhs, ddf_d
     if (!st && cudaStreamSynchronize(s) != cudaSuccess) st = DDF_ERR_CUDA;
     if (best_unit_nnz) *best_unit_nnz = pick;
     return st;
+}
+
+ddf_status ddf_tune_cost(const ddf_csr* A, ddf_kind kind, ddf_opts* o, ddf_stream_t stream, int32_t* pick) {
+    ddf_nvtx_range nvtx_("ddf_tune_cost");
+    if (!A || !o || !A->values || (kind != DDF_SPMV && kind != DDF_SPTRSV)) return DDF_ERR_ARG;
+    // Eq. 1 weight sets (w_op, w_codelet, w_index): the default byte costs, a
+    // cheaper and a dearer codelet, cheaper and dearer offset entries, and
+    // the paper's CPU form
+    static const int64_t cand[][3] = {{8, 32, 4}, {8, 8, 4}, {8, 128, 4}, {8, 32, 1}, {8, 32, 16}, {1, 3, 1}};
+    constexpr int nc = 6;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nin = kind == DDF_SPMV ? A->n_cols : A->n_rows, nout = A->n_rows;
+    double *x = nullptr, *y = nullptr;
+    ddf_status st = ddf_alloc(&x, std::max<int64_t>(nin, 1), s);
+    if (!st) st = ddf_alloc(&y, std::max<int64_t>(nout, 1), s);
+    if (!st && nin > 0) {
+        k_fill_f64<<<ddf_grid(nin, 256, 4096), 256, 0, s>>>(x, nin, 1.0);
+        ddf_count_launch();
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!st && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) st = DDF_ERR_CUDA;
+    float best = 3.0e38f;
+    int32_t win = 0;
+    for (int c = 0; c < nc && !st; ++c) {
+        ddf_opts oc = *o;
+        oc.w_op = cand[c][0];
+        oc.w_codelet = cand[c][1];
+        oc.w_index = cand[c][2];
+        ddf_plan_t p = nullptr;
+        st = ddf_inspect(A, kind, &oc, stream, &p);
+        if (st) break;
+        float ms = 3.0e38f;
+        for (int rep = 0; rep < 4 && !st; ++rep) {   // a warm-up, then the fastest of three
+            cudaEventRecord(e0, s);
+            st = kind == DDF_SPMV ? ddf_spmv(p, x, y, stream) : ddf_sptrsv(p, x, y, stream);
+            cudaEventRecord(e1, s);
+            if (!st && cudaEventSynchronize(e1) != cudaSuccess) st = DDF_ERR_CUDA;
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0 && t < ms) ms = t;
+        }
+        if (!st && kind == DDF_SPTRSV) st = ddf_get_status(p, stream);
+        ddf_plan_destroy(p);
+        if (!st && ms < best) {
+            best = ms;
+            win = c;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    ddf_free(x, s);
+    ddf_free(y, s);
+    if (st) return st;
+    o->w_op = cand[win][0];
+    o->w_codelet = cand[win][1];
+    o->w_index = cand[win][2];
+    if (pick) *pick = win;
+    return cudaStreamSynchronize(s) == cudaSuccess ? DDF_OK : DDF_ERR_CUDA;
 }
 
 }  // extern "C"
