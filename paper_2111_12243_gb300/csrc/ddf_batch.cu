@@ -7,13 +7,16 @@
 // The multi-RHS executors give a row of the block X ([n][nrhs], row-major)
 // to a group of LP lanes: each lane moves VEC consecutive right-hand sides
 // (16 bytes when nrhs = VEC * LP and the blocks are 16-byte aligned, else
-// one element, LP = 32, lane k owning right-hand side k).  A warp runs one
-// matrix row at a time: its G = 32 / LP lane groups take G different points
-// of the row, so one load instruction fetches the X rows of G points, and
-// group g sums the points t = g (mod G).  The G partial sums are combined by
-// a butterfly over the groups, a fixed order, so results do not depend on
-// timing.  A row's points (value, column) are read 32 at a time, lane t
-// loading point t, and handed to the groups with shuffles.
+// one element, LP = 32, lane k owning right-hand side k).  A row of at most
+// SHORT_ROW points runs on one lane group (G = 32 / LP rows per warp at a
+// time); a longer row runs on the whole warp, the G groups taking different
+// points (one load instruction fetches the X rows of G points) and a
+// butterfly over the groups combining their partial sums.  Every order is
+// fixed, so results do not depend on timing.  The solve is a persistent grid
+// of warps taking work items from a ticket; for a batch, its items are the
+// plan's units split per matrix and long rows split into segments, handed out
+// by normalized level (ddf_build_mrhs_items).  ddf_batch_run runs a batch's SpMV
+// and SpTRSV in one launch.
 #include <initializer_list>
 #include <vector>
 
@@ -1172,7 +1175,7 @@ SolveArgs<TV, TX> solve_args(const ddf_plan_s* p, const TV* val, const TX* dinv,
     SolveArgs<TV, TX> A;
     A.n = p->n;
     A.upt = p->mrhs_units_per_ticket > 0 ? p->mrhs_units_per_ticket : 1;
-    if (p->mrhs_q) {   // a batch: the items and order of build_mrhs_order
+    if (p->mrhs_q) {   // a batch: the items and order of ddf_build_mrhs_items
         A.nunits = p->mrhs_nr;
         A.order = p->mrhs_order;
         A.unit_q = p->mrhs_q;
