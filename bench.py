@@ -80,10 +80,10 @@ def parse(argv=None):
                     help="1: everything on one stream; 2: one stream and host thread per matrix; "
                          "4 (default): one per chain, inspect(A)+spmv and inspect(L)+sptrsv of each matrix")
     ap.add_argument("--serial", action="store_true", help="same as --streams 1")
-    ap.add_argument("--prio", default="chain", choices=["chain", "size"],
+    ap.add_argument("--prio", default="chain", choices=["chain", "size", "achain"],
                     help="stream priorities: 'chain' (default) gives the inspect(L) + sptrsv chains the high "
-                         "priority and the inspect(A) + spmv chains the low one; 'size' gives both chains of "
-                         "the largest matrix the high priority")
+                         "priority and the inspect(A) + spmv chains the low one; 'achain' the reverse; 'size' "
+                         "gives both chains of the largest matrix the high priority")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--coarsen", type=int, default=None,
                     help="SpTRSV rows per block (coarsen_rows; 0 = plain level sets; default: library default)")
@@ -326,6 +326,9 @@ def run_ours(args, rank, world, local_rank):
     if args.prio == "chain":
         prio_a = {i: lo_p for i in range(len(D))}
         prio_l = {i: hi_p for i in range(len(D))}
+    elif args.prio == "achain":
+        prio_a = {i: hi_p for i in range(len(D))}
+        prio_l = {i: lo_p for i in range(len(D))}
     else:
         prio_a = prio_l = {i: (hi_p if k == 0 else lo_p) for k, i in enumerate(order)}
     side = [torch.cuda.Stream(device=dev, priority=prio_a[i]) for i in range(len(D))]
@@ -1044,6 +1047,7 @@ def main(argv=None):
                        "l2": "256 MB written then another 256 MB read between steps (the flush's "
                              "write-back happens before the timed work); inputs larger than L2",
                        "priorities": {"chain": "inspect(L)+sptrsv chains high, inspect(A)+spmv chains low",
+                                      "achain": "inspect(A)+spmv chains high, inspect(L)+sptrsv chains low",
                                       "size": "both chains of the largest matrix high"}[args.prio],
                        "streams": {1: "everything on one stream",
                                    2: "one stream and host thread per matrix",
