@@ -215,6 +215,109 @@ def test_validation_errors(rows, n_cols, kind, code):
     assert e.value.status == code
 
 
+def _ragged(n, seed, lower):
+    """Random CSR with rows of 0 to 100 sorted distinct columns (a few empty
+    rows), so that rows and their pairs fall across 32-entry steps; lower:
+    columns below the row, then the diagonal (values 1 off it, 4 on it)."""
+    rng = np.random.default_rng(seed)
+    rows = []
+    for i in range(n):
+        m = int(rng.integers(0, 101)) if rng.random() > 0.05 else 0
+        if lower:
+            cols = np.unique(rng.integers(0, i, m)) if i > 0 else np.zeros(0, np.int64)
+            rows.append(list(cols) + [i])
+        else:
+            rows.append(list(np.unique(rng.integers(0, n, m))))
+    rp = np.zeros(n + 1, np.int32)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    ci = np.array([c for r in rows for c in r], np.int32)
+    v = np.ones(ci.size)
+    if lower:
+        v[rp[1:] - 1] = 4.0
+    return synth.CSR(n, n, rp, ci, v)
+
+
+def _plant(a, k, col):
+    b = synth.CSR(a.n_rows, a.n_cols, a.rowptr.copy(), a.colidx.copy(), a.values.copy())
+    b.colidx[k] = col
+    return b
+
+
+def _straddling_pair(a):
+    """An entry k with k % 32 == 31 whose successor is in the same row."""
+    rp = a.rowptr
+    for k in range(31, a.colidx.size - 1, 32):
+        r = int(np.searchsorted(rp, k, side="right")) - 1
+        if k + 1 < rp[r + 1]:
+            return k
+    raise AssertionError("no straddling pair")
+
+
+@pytest.mark.parametrize("case", ["clean", "swap_straddling", "dup_straddling", "last_out_of_range",
+                                  "negative_mid", "both"])
+def test_validation_of_ragged_rows(case):
+    # The CSR check streams each block of 32 rows in 32-entry steps: faults at
+    # a step boundary, in the last entry and in the middle must all be found,
+    # and descending columns across a row boundary must not be flagged.
+    a = _ragged(3001, 11, lower=False)
+    n, nnz = a.n_rows, a.colidx.size
+    k = _straddling_pair(a)
+    if case == "clean":
+        b, code = a, 0
+    elif case == "swap_straddling":
+        b, code = _plant(a, k, a.colidx[k + 1]), 3
+        b.colidx[k + 1] = a.colidx[k]
+    elif case == "dup_straddling":
+        b, code = _plant(a, k + 1, a.colidx[k]), 3
+    elif case == "last_out_of_range":
+        b, code = _plant(a, nnz - 1, n), 4
+    elif case == "negative_mid":   # the first entry of a middle row: the row stays sorted
+        r = int(np.nonzero(np.diff(a.rowptr)[n // 2:] > 0)[0][0]) + n // 2
+        b, code = _plant(a, int(a.rowptr[r]), -1), 4
+    else:
+        b, code = _plant(a, nnz - 1, n), 3
+        b.colidx[k + 1] = a.colidx[k]
+    if code == 0:
+        inspect(b, 1).destroy()
+        return
+    with pytest.raises(ddf.DDFError) as e:
+        inspect(b, 1)
+    assert e.value.status == code
+
+
+@pytest.mark.parametrize("case,code", [("clean", 0), ("missing_diag_last_row", 6), ("above_diag", 5),
+                                       ("zero_diag", 7), ("empty_row", 6)])
+def test_validation_of_ragged_lower(case, code):
+    a = _ragged(1001, 12, lower=True)   # 1001 rows: the last warp of rows is partial
+    n, rp = a.n_rows, a.rowptr
+    b = synth.CSR(n, n, rp.copy(), a.colidx.copy(), a.values.copy())
+    if case == "missing_diag_last_row":   # drop the last row's diagonal
+        m = b.colidx.size - 1
+        nrp = rp.copy()
+        nrp[n] = m
+        b = synth.CSR(n, n, nrp, b.colidx[:m].copy(), b.values[:m].copy())
+    elif case == "above_diag":
+        r = 500
+        b.colidx[rp[r + 1] - 1] = r + 1
+    elif case == "zero_diag":
+        b.values[rp[700] - 1] = 0.0
+    elif case == "empty_row":
+        r = 999
+        keep = np.ones(b.colidx.size, bool)
+        keep[rp[r]:rp[r + 1]] = False
+        cnt = np.diff(rp)
+        cnt[r] = 0
+        nrp = np.zeros(n + 1, np.int32)
+        nrp[1:] = np.cumsum(cnt)
+        b = synth.CSR(n, n, nrp, b.colidx[keep], b.values[keep])
+    if code == 0:
+        inspect(b, 2).destroy()
+        return
+    with pytest.raises(ddf.DDFError) as e:
+        inspect(b, 2)
+    assert e.value.status == code
+
+
 def test_zero_diagonal_rejected():
     a = csr([[0], [0, 1]], 2, [1.0, 1.0, 0.0])
     with pytest.raises(ddf.DDFError) as e:
