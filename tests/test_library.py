@@ -89,3 +89,46 @@ def test_host_argument_errors_without_gpu(libpath):
     assert L.ddf_spmv(None, None, None, None) == 1
     assert L.ddf_sptrsv(None, None, None, None) == 1
     assert L.ddf_last_launches(None) == 0
+
+
+def test_every_entry_point_rejects_missing_handles_without_gpu(libpath):
+    # Argument checks come before any CUDA call, so they run here without a GPU
+    L = ddf.lib()
+    ARG, TOO_LARGE = 1, 13
+    sz = ctypes.c_size_t(0)
+    i32 = ctypes.c_int32(0)
+    i64 = ctypes.c_int64(0)
+    h = ctypes.c_void_p()
+    assert L.ddf_update_values(None, None, 1, None) == ARG
+    assert L.ddf_get_status(None, None) == ARG
+    assert L.ddf_plan_stats(None, None) == ARG
+    assert L.ddf_plan_export(None, None, ctypes.byref(i64), None, None, ctypes.byref(i32), None) == ARG
+    assert L.ddf_debug_set_dependency(None, 0, 0) == ARG
+    assert L.ddf_spmv_lowp(None, None, None, 1, None) == ARG
+    assert L.ddf_sptrsv_refine(None, None, None, 1e-12, 10, None, None, None) == ARG
+    assert L.ddf_plan_validate(None) == ARG
+    assert L.ddf_plan_save(None, None, ctypes.byref(sz)) == ARG
+    # loading: no buffer, a buffer too short for the header, a wrong magic, no output handle
+    assert L.ddf_plan_load(None, 0, None, ctypes.byref(h)) == ARG
+    junk = ctypes.create_string_buffer(b"x" * 4096)
+    assert L.ddf_plan_load(junk, 8, None, ctypes.byref(h)) == ARG
+    assert L.ddf_plan_load(junk, 4096, None, ctypes.byref(h)) == ARG
+    assert L.ddf_plan_load(junk, 4096, None, None) == ARG
+    # batches and several right-hand sides
+    A = ddf.ddf_csr()
+    assert L.ddf_inspect_batch(None, 2, 1, None, None, ctypes.byref(h)) == ARG
+    assert L.ddf_inspect_batch(ctypes.byref(A), 0, 1, None, None, ctypes.byref(h)) == ARG
+    assert L.ddf_inspect_batch(ctypes.byref(A), 1, 3, None, None, ctypes.byref(h)) == ARG
+    assert L.ddf_inspect_batch(ctypes.byref(A), 1, 1, None, None, None) == ARG
+    assert L.ddf_spmm(None, None, None, 32, 1, None) == ARG
+    assert L.ddf_sptrsm(None, None, None, 32, 1, None) == ARG
+    assert L.ddf_batch_run(None, None, None, None, None, None, 32, 1, None) == ARG
+    assert L.ddf_tune(None, None, None, 32, 1, None, ctypes.byref(i32)) == ARG
+    o = ddf.ddf_opts_default()
+    assert L.ddf_tune_cost(None, 1, ctypes.byref(o), None, ctypes.byref(i32)) == ARG
+    assert L.ddf_tune_cost(ctypes.byref(A), 1, ctypes.byref(o), None, ctypes.byref(i32)) == ARG   # no values
+    assert L.ddf_tune_cost(ctypes.byref(A), 3, ctypes.byref(o), None, ctypes.byref(i32)) == ARG
+    # the allocation-free solve: bad sizes and limits, then a size beyond its scratch
+    assert L.ddf_sptrsv_csr_noalloc(-1, 0, None, None, None, None, None, 1000, None) == ARG
+    assert L.ddf_sptrsv_csr_noalloc(4, 4, None, None, None, None, None, 0, None) == ARG
+    assert L.ddf_sptrsv_csr_noalloc((1 << 20) + 1, 0, None, None, None, None, None, 1000, None) == TOO_LARGE
